@@ -1,0 +1,433 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics
+(closed forms, a published generator, a textbook exponential, brute force),
+independent of the oracle's own code paths."""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import synth
+from oracle import dense, gates, mps, noise, robust
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+I2 = np.eye(2)
+PX = np.array([[0, 1], [1, 0]], dtype=complex)
+PY = np.array([[0, -1j], [1j, 0]])
+PZ = np.diag([1.0, -1.0]).astype(complex)
+
+
+def mkpb(N, K, dt, C, chi, u, mask, J, inputs, targets, g_fixed=None, eps=1e-12):
+    return robust.Problem(N=N, K=K, dt=dt, C=C, chi=chi, u=u, mask=mask, J=np.atleast_2d(J),
+                          inputs=[m.sites for m in inputs], targets=[m.sites for m in targets],
+                          g_fixed=g_fixed, eps=eps)
+
+
+def rand_products(N, P, seed):
+    return synth.product_inputs(N, P, seed)
+
+
+# ---------------------------------------------------------------- (a) pi pulse
+def test_pi_pulse_gives_parallel_x():
+    N, K, dt = 6, 10, 0.1
+    u = synth.pi_pulse_controls(K, 2, N, dt)
+    ins = rand_products(N, 3, 5)
+    pb = mkpb(N, K, dt, 2, 16, u, synth.control_mask(2, N), np.zeros(N - 1), ins, synth.x_targets(ins))
+    F, g, _ = robust.ensemble(pb)
+    assert abs(F - 1.0) < 1e-13
+    # a maximum: gradient vanishes
+    assert np.max(np.abs(g)) < 1e-12
+    o, _ = dense.trajectory(pb, 0, 1, False)
+    assert abs(abs(o) - 1.0) < 1e-13
+
+
+# ---------------------------------------------------- J = 0: single-qubit closed form
+def _rot(x, y, dt):
+    """exp(-i dt (x X + y Y)) = cos(th) I - i sin(th)/th (a X + b Y), th = |(a, b)|."""
+    a, b = dt * x, dt * y
+    th = math.hypot(a, b)
+    sc = math.sin(th) / th if th > 0 else 1.0
+    return math.cos(th) * I2 - 1j * sc * (a * PX + b * PY)
+
+
+def _drot(x, y, dt, wrt):
+    a, b = dt * x, dt * y
+    th = math.hypot(a, b)
+    sc = math.sin(th) / th
+    dsc = (th * math.cos(th) - math.sin(th)) / th ** 2
+    da = a / th if wrt == "x" else b / th
+    gen = PX if wrt == "x" else PY
+    dU = -math.sin(th) * da * I2 - 1j * (dsc * da * (a * PX + b * PY) + sc * gen)
+    return dt * dU
+
+
+def test_zero_crosstalk_closed_form_fidelity_and_gradient():
+    N, K, dt = 5, 6, 0.1
+    rng = np.random.default_rng(11)
+    u = rng.normal(0, 0.7, size=(K, 2, N))
+    ins = rand_products(N, 1, 12)
+    tgs = rand_products(N, 1, 13)
+    pb = mkpb(N, K, dt, 2, 8, u, synth.control_mask(2, N), np.zeros(N - 1), ins, tgs)
+    F, g, _ = robust.ensemble(pb)
+    vin = [s.reshape(2) for s in ins[0].sites]
+    vt = [s.reshape(2) for s in tgs[0].sites]
+    Us = []
+    Os = []
+    for i in range(N):
+        U = I2.astype(complex)
+        for k in range(K):
+            U = _rot(u[k, 0, i], u[k, 1, i], dt) @ U
+        Us.append(U)
+        Os.append(np.vdot(vt[i], U @ vin[i]))
+    O = np.prod(Os)
+    assert abs(F - abs(O) ** 2) < 1e-13
+    gref = np.zeros((K, 2, N))
+    for i in range(N):
+        rest = np.prod([Os[j] for j in range(N) if j != i])
+        for k in range(K):
+            for c, wrt in ((0, "x"), (1, "y")):
+                M = I2.astype(complex)
+                for kk in range(K):
+                    M = (_drot(u[kk, 0, i], u[kk, 1, i], dt, wrt) if kk == k else
+                         _rot(u[kk, 0, i], u[kk, 1, i], dt)) @ M
+                dO = rest * np.vdot(vt[i], M @ vin[i])
+                gref[k, c, i] = 2 * np.real(np.conj(O) * dO)
+    assert np.max(np.abs(g - gref)) < 1e-12 * max(1.0, np.max(np.abs(gref))) + 1e-15
+
+
+# ---------------------------------------------------------- ZZ only: closed form
+def test_zz_only_closed_form_with_g_gradient():
+    N, K, dt = 6, 5, 0.2
+    rng = np.random.default_rng(21)
+    u = rng.normal(0, 0.8, size=(K, 3, N))
+    mask = synth.control_mask(3, N, "all")
+    mask[0, :] = 0
+    mask[1, :] = 0
+    J = rng.uniform(-0.3, 0.3, size=N - 1)
+    ins = rand_products(N, 1, 22)
+    tgs = rand_products(N, 1, 23)
+    pb = mkpb(N, K, dt, 3, 8, u, mask, J, ins, tgs)
+    F, g, _ = robust.ensemble(pb)
+    vin = [s.reshape(2) for s in ins[0].sites]
+    vt = [s.reshape(2) for s in tgs[0].sites]
+    sig = np.array([1.0, -1.0])
+    phi = np.array([dt * (u[:, 2, b].sum() + K * J[b]) for b in range(N - 1)])
+
+    def chain(deriv=None):
+        w = np.conj(vt[0]) * vin[0]
+        for b in range(N - 1):
+            Mb = np.exp(-1j * phi[b] * np.outer(sig, sig))
+            if deriv == b:
+                Mb = Mb * (-1j * dt * np.outer(sig, sig))
+            w = (w @ Mb) * np.conj(vt[b + 1]) * vin[b + 1]
+        return w.sum()
+
+    O = chain()
+    assert abs(F - abs(O) ** 2) < 1e-13
+    for b in range(N - 1):
+        dO = chain(deriv=b)
+        for k in range(K):
+            assert abs(g[k, 2, b] - 2 * np.real(np.conj(O) * dO)) < 1e-12
+    assert np.all(g[:, :2, :] == 0.0)
+    assert np.all(g[:, 2, N - 1] == 0.0)
+
+
+# ------------------------------------------------ untruncated MPS == dense vector
+def test_untruncated_mps_equals_dense_statevector():
+    N, K, dt = 8, 4, 0.15
+    rng = np.random.default_rng(31)
+    u = rng.normal(0, 0.8, size=(K, 3, N))
+    J = rng.uniform(-0.2, 0.2, size=(2, N - 1))
+    ins = rand_products(N, 2, 32)
+    tgs = rand_products(N, 2, 33)
+    pb = mkpb(N, K, dt, 3, 16, u, synth.control_mask(3, N, "all"), J, ins, tgs)
+    for s in range(2):
+        for p in range(2):
+            o1, d1 = robust.trajectory(pb, s, p)
+            o2, d2 = dense.trajectory(pb, s, p)
+            assert abs(o1 - o2) < 1e-12
+            assert np.max(np.abs(d1 - d2)) < 1e-12
+
+
+def test_mps_state_matches_dense_vector_elementwise():
+    N, K, dt = 6, 3, 0.3
+    rng = np.random.default_rng(41)
+    u = rng.normal(0, 1.0, size=(K, 3, N))
+    ins = rand_products(N, 1, 42)
+    pb = mkpb(N, K, dt, 3, 8, u, synth.control_mask(3, N, "all"), rng.normal(0, 0.1, N - 1), ins, ins)
+    B, lam = mps.canonicalize(pb.inputs[0], pb.chi, pb.eps)
+    a = dense.mps_vector(pb.inputs[0])
+    for (k, par, tau) in robust.layers(K, dt):
+        for b in range(par, N - 1, 2):
+            G, _, _ = robust.bond_gate(pb, 0, k, b, tau)
+            mps.two_site_update(B, lam, b, G, pb.chi, pb.eps)
+            a = dense.apply_two_site(a, G, b, N)
+    v = mps.to_dense(B)
+    assert np.max(np.abs(v - a)) < 1e-12
+    # Schmidt values of every bond = singular values of the dense reshape
+    for b in range(N - 1):
+        sv = np.linalg.svd(a.reshape(2 ** (b + 1), -1), compute_uv=False)
+        k = len(lam[b])
+        assert np.max(np.abs(sv[:k] - lam[b])) < 1e-12
+        assert np.all(sv[k:] < 1e-12)
+
+
+# ------------------------------------------------------- Trotter error is O(dt^2)
+def test_second_order_trotter_error_scaling():
+    N, K0, T = 4, 2, 1.0
+    rng = np.random.default_rng(51)
+    u0 = rng.normal(0, 1.0, size=(K0, 3, N))
+    J = rng.uniform(-0.5, 0.5, size=N - 1)
+    ins = rand_products(N, 1, 52)
+    tgs = rand_products(N, 1, 53)
+    errs = []
+    for r in (4, 8, 16):
+        u = np.repeat(u0, r, axis=0)
+        K = K0 * r
+        pb = mkpb(N, K, T / K, 3, 16, u, synth.control_mask(3, N, "all"), J, ins, tgs)
+        o_t, _ = dense.trajectory(pb, 0, 0, False)
+        o_e = dense.exact_overlap(pb, 0, 0)
+        errs.append(abs(o_t - o_e))
+    assert 3.3 < errs[0] / errs[1] < 4.7
+    assert 3.3 < errs[1] / errs[2] < 4.7
+
+
+# ------------------------------------------------------- finite differences
+def test_gradient_matches_central_finite_differences():
+    N, K, dt = 6, 5, 0.1
+    rng = np.random.default_rng(61)
+    u = rng.normal(0, 0.5, size=(K, 3, N))
+    mask = synth.control_mask(3, N, "all")
+    J = rng.uniform(-0.1, 0.1, size=(2, N - 1))
+    ins = rand_products(N, 2, 62)
+    tgs = synth.x_targets(ins)
+    pb = mkpb(N, K, dt, 3, 8, u, mask, J, ins, tgs)
+    F, g, _ = robust.ensemble(pb)
+    h = 1e-6
+    idxs = [tuple(int(rng.integers(0, n)) for n in u.shape) for _ in range(20)]
+    for idx in idxs:
+        up, um = u.copy(), u.copy()
+        up[idx] += h
+        um[idx] -= h
+        Fp, _, _ = robust.ensemble(mkpb(N, K, dt, 3, 8, up, mask, J, ins, tgs), want_grad=False)
+        Fm, _, _ = robust.ensemble(mkpb(N, K, dt, 3, 8, um, mask, J, ins, tgs), want_grad=False)
+        fd = (Fp - Fm) / (2 * h)
+        assert abs(fd - g[idx]) < 1e-6 * max(1e-3, np.max(np.abs(g)))
+
+
+# ----------------------------------------- Daleckii-Krein vs Van Loan block exponential
+@pytest.mark.parametrize("degenerate", [False, True])
+def test_gate_derivative_matches_block_exponential(degenerate):
+    rng = np.random.default_rng(71 + degenerate)
+    if degenerate:
+        h = 0.7 * np.kron(PZ, PZ)
+    else:
+        a = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
+        h = (a + a.conj().T) / 2
+    b = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
+    P = (b + b.conj().T) / 2
+    tau = 0.37
+    G, lam, V = gates.expm_hermitian(h, tau)
+    assert np.max(np.abs(G - scipy.linalg.expm(-1j * tau * h))) < 1e-14
+    assert np.max(np.abs(G.conj().T @ G - np.eye(4))) < 1e-14
+    big = np.zeros((8, 8), dtype=complex)
+    big[:4, :4] = -1j * tau * h
+    big[4:, 4:] = -1j * tau * h
+    big[:4, 4:] = -1j * tau * P
+    ref = scipy.linalg.expm(big)[:4, 4:]
+    dG = gates.dexpm_hermitian(lam, V, tau, P)
+    assert np.max(np.abs(dG - ref)) < 1e-13
+
+
+def test_bond_hamiltonians_sum_to_system_hamiltonian():
+    N = 5
+    rng = np.random.default_rng(81)
+    x, y, c = rng.normal(size=N), rng.normal(size=N), rng.normal(size=N - 1)
+    H = np.zeros((2 ** N, 2 ** N), dtype=complex)
+    for b in range(N - 1):
+        h = gates.bond_hamiltonian(N, b, x[b], y[b], x[b + 1], y[b + 1], c[b])
+        H += np.kron(np.kron(np.eye(2 ** b), h), np.eye(2 ** (N - b - 2)))
+
+    def op(o, i):
+        return np.kron(np.kron(np.eye(2 ** i), o), np.eye(2 ** (N - i - 1)))
+
+    ref = sum(x[i] * op(PX, i) + y[i] * op(PY, i) for i in range(N))
+    ref = ref + sum(c[b] * op(PZ, b) @ op(PZ, b + 1) for b in range(N - 1))
+    assert np.max(np.abs(H - ref)) < 1e-13
+
+
+# ----------------------------------------------------------------- invariants
+def test_costate_overlap_is_constant_over_layers():
+    N, K, dt = 6, 4, 0.2
+    rng = np.random.default_rng(91)
+    u = rng.normal(0, 0.8, size=(K, 3, N))
+    ins = rand_products(N, 1, 92)
+    tgs = rand_products(N, 1, 93)
+    pb = mkpb(N, K, dt, 3, 8, u, synth.control_mask(3, N, "all"), rng.normal(0, .1, N - 1), ins, tgs)
+    sched = robust.layers(K, dt)
+    B, lam = mps.canonicalize(pb.inputs[0], 8, 1e-12)
+    states = [[x.copy() for x in B]]
+    gl = []
+    for (k, par, tau) in sched:
+        gg = {}
+        for b in range(par, N - 1, 2):
+            G, _, _ = robust.bond_gate(pb, 0, k, b, tau)
+            gg[b] = G
+            mps.two_site_update(B, lam, b, G, 8, 1e-12)
+        gl.append(gg)
+        states.append([x.copy() for x in B])
+    C, clam = mps.canonicalize(pb.targets[0], 8, 1e-12)
+    vals = [mps.overlap(C, states[-1])]
+    for li in range(len(sched) - 1, -1, -1):
+        for b, G in gl[li].items():
+            mps.two_site_update(C, clam, b, G.conj().T, 8, 1e-12)
+        vals.append(mps.overlap(C, states[li]))
+        # norms stay 1
+        assert abs(mps.overlap(C, C) - 1) < 1e-12
+    assert np.max(np.abs(np.array(vals) - vals[0])) < 1e-12
+
+
+def test_identical_samples_give_single_sample_result():
+    N, K, dt = 5, 3, 0.2
+    rng = np.random.default_rng(95)
+    u = rng.normal(0, 0.6, size=(K, 2, N))
+    J1 = rng.uniform(-0.1, 0.1, size=(1, N - 1))
+    ins = rand_products(N, 1, 96)
+    tgs = synth.x_targets(ins)
+    F1, g1, _ = robust.ensemble(mkpb(N, K, dt, 2, 8, u, synth.control_mask(2, N), J1, ins, tgs))
+    F3, g3, _ = robust.ensemble(mkpb(N, K, dt, 2, 8, u, synth.control_mask(2, N), np.repeat(J1, 3, 0), ins, tgs))
+    assert abs(F1 - F3) < 1e-15 and np.max(np.abs(g1 - g3)) < 1e-15
+
+
+def test_truncated_fidelity_converges_in_chi():
+    N, K, dt = 10, 6, 0.25
+    rng = np.random.default_rng(97)
+    u = rng.normal(0, 1.5, size=(K, 3, N))
+    mask = synth.control_mask(3, N, "all")
+    ins = rand_products(N, 1, 98)
+    tgs = rand_products(N, 1, 99)
+    J = rng.normal(0, 0.1, size=N - 1)
+    o_exact, _ = dense.trajectory(mkpb(N, K, dt, 3, 32, u, mask, J, ins, tgs), 0, 0, False)
+    errs = []
+    for chi in (4, 8, 16, 32):
+        o, _ = robust.trajectory(mkpb(N, K, dt, 3, chi, u, mask, J, ins, tgs), 0, 0, False)
+        errs.append(abs(o - o_exact))
+    assert errs[-1] < 1e-12
+    assert errs[0] > errs[1] > errs[2] > errs[3]
+
+
+# ------------------------------------------------------------------ canonical form
+def test_canonical_form_of_random_mps():
+    rng = np.random.default_rng(101)
+    N, D = 6, 3
+    dims = [1] + [D] * (N - 1) + [1]
+    sites = [rng.normal(size=(dims[i], 2, dims[i + 1])) + 1j * rng.normal(size=(dims[i], 2, dims[i + 1]))
+             for i in range(N)]
+    v = dense.mps_vector(sites)
+    B, lam = mps.canonicalize(sites, 64, 1e-12)
+    w = mps.to_dense(B)
+    assert abs(abs(np.vdot(v, w)) - 1.0) < 1e-13
+    for i in range(1, N):
+        b = B[i]
+        gram = sum(b[:, s, :] @ b[:, s, :].conj().T for s in range(2))
+        assert np.max(np.abs(gram - np.eye(b.shape[0]))) < 1e-13
+    for bnd in range(N - 1):
+        sv = np.linalg.svd(v.reshape(2 ** (bnd + 1), -1), compute_uv=False)
+        assert np.max(np.abs(sv[:len(lam[bnd])] - lam[bnd])) < 1e-13
+
+
+# --------------------------------------------------------------------- noise
+def test_splitmix64_published_vectors():
+    for line in open(os.path.join(GOLD, "splitmix64.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        seed, i, out = (int(x) for x in line.split())
+        assert noise.splitmix64(seed, i) == out
+
+
+def test_noise_distributions():
+    J = noise.sample_J(5, 400, 51, 0, 0.1)
+    assert J.shape == (400, 50) and np.all(np.abs(J) <= 0.1)
+    assert abs(J.mean()) < 0.002 and abs(J.var() - 0.01 / 3) < 2e-4
+    Jn = noise.sample_J(6, 400, 51, 1, 0.05)
+    assert abs(Jn.mean()) < 0.002 and abs(Jn.std() - 0.05) < 0.002
+    # bond (s, b) uses counter s*(N-1)+b: the stream is the same for a longer ensemble
+    assert np.array_equal(noise.sample_J(5, 3, 51, 0, 0.1), J[:3])
+
+
+# ------------------------------------------------------------------- targets
+def _read_ghz_golden():
+    rows = {}
+    for line in open(os.path.join(GOLD, "ghz_sec4.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        kind, s, r, c, v = line.split()
+        rows[(kind, int(s), int(r), int(c))] = float(v)
+    return rows
+
+
+def test_ghz_mps_is_the_papers_and_is_ghz():
+    gold = _read_ghz_golden()
+    N = 7
+    m = synth.ghz_mps(N)
+    for (kind, s, r, c), v in gold.items():
+        t = {"first": m.sites[0][0], "mid": m.sites[1], "last": m.sites[-1][:, :, 0]}[kind]
+        if kind == "first":
+            assert t[s, c] == v
+        elif kind == "mid":
+            assert t[r, s, c] == v
+        else:
+            assert t[r, s] == v
+    psi = mps.to_dense(m.sites)
+    assert abs(np.vdot(psi, psi) - 1) < 1e-15
+    ref = np.zeros(2 ** N)
+    ref[0] = ref[-1] = 2 ** -0.5
+    assert np.max(np.abs(psi - ref)) < 1e-15
+
+
+def test_cnot_targets_match_dense_cnots():
+    N = 6
+    ins = rand_products(N, 2, 111)
+    tg = synth.cnot_targets(ins)
+    cnot = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=complex)
+    for a, t in zip(ins, tg):
+        v = dense.mps_vector(a.sites)
+        for i in range(0, N, 2):
+            v = dense.apply_two_site(v, cnot, i, N)
+        w = mps.to_dense(t.sites)
+        assert np.max(np.abs(v - w)) < 1e-15
+
+
+def _heisenberg_dense(N):
+    H = np.zeros((2 ** N, 2 ** N), dtype=complex)
+    for b in range(N - 1):
+        for P in (PX, PY, PZ):
+            H += np.kron(np.kron(np.eye(2 ** b), np.kron(P, P)), np.eye(2 ** (N - b - 2)))
+    return H
+
+
+def test_heisenberg_ground_state():
+    _, e2, _ = synth.heisenberg_ground_mps(2, 20)
+    assert abs(e2 + 3.0) < 1e-12          # the singlet
+    for N in (8, 10):
+        m, e0, psi = synth.heisenberg_ground_mps(N, 64)
+        w = np.linalg.eigvalsh(_heisenberg_dense(N))
+        assert abs(e0 - w[0]) < 1e-9
+        assert w[1] - w[0] > 1e-3        # unique ground state for even N
+        v = mps.to_dense(m.sites)
+        assert abs(abs(np.vdot(v, psi)) - 1) < 1e-10
+    # compressed to D = 4 at N = 10: overlap >= 1 - discarded weight (loose)
+    m4, _, psi = synth.heisenberg_ground_mps(10, 4)
+    v4 = mps.to_dense(m4.sites)
+    assert 0.9 < abs(np.vdot(v4, psi)) < 1.0
+
+
+def test_per_gate_infidelity_printed_values():
+    for line in open(os.path.join(GOLD, "per_gate_infidelity.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        gate, n, chib, printed = line.split()
+        q = 1 if gate == "X" else 2
+        val = robust.per_gate_infidelity(float(chib), int(n), q)
+        assert abs(val - float(printed)) < 0.06 * float(printed)
