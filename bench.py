@@ -1,0 +1,312 @@
+"""Benchmark: fwd+adjoint MPS slice-steps/s of the tensor-network robust
+GRAPE hot path (ensemble fidelity + costate gradient) on the parallel-CNOT
+workload N = 50, chi_max = 64, K = 100, M = 256, P = 8, C = 3.
+
+One step = one full evaluation through the C ABI on device-resident inputs:
+noise draw (device SplitMix64), gate build, forward TEBD of all M*P
+trajectories with checkpoints, overlaps, costate sweep with environments and
+gradient, and the fixed-order ensemble reduction.  value = M*P*K slice-steps
+per second (whole job; N GPUs each evaluate their own shard of noise samples).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
+
+--impl reference times the CPU oracle (NumPy/LAPACK) on the host cores on a
+bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+DEFAULT_WORKLOAD = "cnot50"
+METRIC = "fwd+adjoint MPS slice-steps/s (N=50,chi=64,M=256)"
+UNIT = "slice-steps/s"
+SM_COUNT = 152
+FP64_FMA_PER_CLK_PER_SM = 2        # GB300: 1.25 TFLOP/s FP64 nominal at 2070 MHz x 152 SMs
+SM_MAX_MHZ = 2070.0
+REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+               0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+
+def fp64_peak_tflops():
+    """FP64 FMA peak derived from unit counts and the maximum SM clock."""
+    return 2.0 * FP64_FMA_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def workload_config(w):
+    return {"workload": "%s: %s on N=%d, chi_max=%d, K=%d, dt=%g, C=%d, M=%d, P=%d, %s J, controls N(0,%g^2)"
+                        % (w.name, {"x": "parallel X", "cnot": "parallel CNOT", "ghz": "GHZ preparation",
+                                    "heisenberg": "Heisenberg ground state"}[w.target],
+                           w.N, w.chi, w.K, w.dt, w.C, w.M, w.P,
+                           ("U[-%g,%g]" % (w.noise_scale, w.noise_scale)) if w.noise_dist == 0
+                           else ("N(0,%g^2)" % w.noise_scale), w.u_sigma),
+            "N": w.N, "chi_max": w.chi, "K": w.K, "M": w.M, "P": w.P, "C": w.C, "dt": w.dt,
+            "slice_steps_per_eval": w.slice_steps}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 4:
+                try:
+                    self.rows.append((float(parts[0]), float(parts[1]), float(parts[2]), int(parts[3], 16)))
+                except ValueError:
+                    pass
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        busy = [r for r in self.rows if not (r[3] & 0x1)] or self.rows
+        reasons = set()
+        for r in busy:
+            for bit, name in REASON_BITS.items():
+                if r[3] & bit and bit != 0x1:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in busy), "sm_max_mhz": max(r[1] for r in busy),
+                "power_w_max": max(r[2] for r in busy), "samples": len(busy), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------------
+# CPU oracle leg
+# --------------------------------------------------------------------------
+
+def oracle_sample(w, n_traj, K_s, workers):
+    """Time the oracle (fwd + costate gradient) on n_traj trajectories of the
+    first K_s slices of workload w, one trajectory per spawn worker."""
+    from oracle import noise, robust, runner
+    ws = w.replace(K=K_s)
+    prob = synth.make_problem(ws)
+    J = noise.sample_J(w.seed_J, n_traj, w.N, w.noise_dist, w.noise_scale)
+    pb = robust.from_workload(prob, J)
+    pairs = [(s, 0) for s in range(n_traj)]
+    _, secs, used = runner.run(pb, pairs, want_grad=True, workers=workers)
+    return n_traj * K_s, secs, used
+
+
+def cpu_baseline(w, budget_steps=1):
+    workers = os.cpu_count() or 1
+    units, secs, used = oracle_sample(w, workers, w.K, workers)
+    return {"value": units / secs, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": "%d trajectories (noise samples 0..%d, input 0) x all %d slices, fwd+adjoint, "
+                      "one per spawn worker, OMP/BLAS 1 thread each: %.1f s" % (used, used - 1, w.K, secs)}
+
+
+def reference_arm(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    workers = os.cpu_count() or 1
+    total = args.steps + args.warmup
+    K_s = w.K if total <= 6 else max(5, (6 * w.K) // total)
+    for _ in range(args.warmup):
+        oracle_sample(w, workers, K_s, workers)
+    times, units = [], 0
+    for _ in range(args.steps):
+        u, secs, used = oracle_sample(w, workers, K_s, workers)
+        times.append(secs)
+        units += u
+    tot = sum(times)
+    value = units / tot
+    sample = ("%d trajectories x first %d of %d slices per step, fwd+adjoint, one per spawn worker "
+              "(OMP/BLAS 1 thread each)" % (workers, K_s, w.K))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": workload_config(w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GPU leg
+# --------------------------------------------------------------------------
+
+def gpu_arm(args, w):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_03639_gb300 import Context
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ins, tgs = w.states()
+    mask = w.mask()
+    u = w.controls()
+    ctx = Context(w.N, w.K, w.dt, w.chi, w.M, w.C, ins, tgs, cutoff=w.sv_cutoff, mask=mask,
+                  stream=stream.cuda_stream)
+    u_dev = torch.tensor(u, dtype=torch.float64, device=dev)
+    F_dev = torch.zeros(1, dtype=torch.float64, device=dev)
+    g_dev = torch.zeros(u.shape, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    seed0 = w.seed_J + 1000003 * rank           # each rank draws its own noise shard
+
+    def step(i):
+        ctx.set_controls_dev(u_dev.data_ptr())
+        ctx.sample_noise(seed0 + i, w.noise_dist, w.noise_scale)
+        ctx.evaluate_dev(F_dev.data_ptr(), g_dev.data_ptr())
+
+    for i in range(args.warmup):
+        step(i)
+    ctx.sync()
+    ctx.stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    per_step, alg, traj_ms, launches = [], 0.0, 0.0, 0
+    hist = np.zeros(w.chi + 1, dtype=np.int64)
+    disc, sweeps, updates, maxb = 0.0, 0, 0, 0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()                      # evict L2 (129 MB) between timed steps
+            ev[i][0].record(stream)
+            step(args.warmup + i)
+            ev[i][1].record(stream)
+            ev[i][1].synchronize()
+            per_step.append(ev[i][0].elapsed_time(ev[i][1]))
+            st = ctx.stats()
+            ctx.sync()
+            alg += st["alg_flops"]
+            traj_ms += st["traj_ms"]
+            launches += st["traj_launches"]
+            hist += np.asarray(st["bond_hist"], dtype=np.int64)
+            disc += st["discarded_weight"]
+            sweeps += st["jacobi_sweeps"]
+            updates += st["updates"]
+            maxb = max(maxb, st["max_bond"])
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ms = sum(per_step)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * w.slice_steps / (ms_per_step / 1000.0)
+
+    # end to end through the host-buffer C ABI: controls in, F and gradient out
+    u_pin = torch.tensor(u, dtype=torch.float64).pin_memory().numpy()
+    e2e_steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        ctx.set_controls(u_pin)
+        ctx.sample_noise(seed0 + 7919 + i, w.noise_dist, w.noise_scale)
+        ctx.fidelity_grad()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    KCN = w.K * w.C * w.N
+
+    peak = fp64_peak_tflops()
+    achieved = (alg / launches) / (traj_ms / launches / 1000.0) / 1e12 if launches else None
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traj_kernel_traffic.json")
+    if os.path.exists(prof):
+        try:
+            pj = json.load(open(prof))
+            if pj.get("workload") == w.name and pj.get("bytes_per_launch"):
+                traffic = pj["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload_config(w), parallelism="ensemble-sharded x%d (noise samples per GPU)" % world,
+                       l2="flushed between timed steps (512 MB write, outside the per-step events)"),
+        "e2e": {"value": world * w.slice_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": KCN * 8,
+                "d2h_bytes_per_step": 8 + KCN * 8},
+        "gpu_launches": 5 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "kernel": "tnrc::traj_kernel", "peak_source": "derived FP64 FMA peak: 2 DFMA/clk/SM x 152 SMs x 2070 MHz"},
+        "clocks": clk.summary(),
+        "workload_stats": {"alg_flops_per_step": alg / args.steps, "traj_kernel_ms_per_step": traj_ms / args.steps,
+                           "max_bond": maxb, "bond_hist": hist.tolist(), "discarded_weight": disc / args.steps,
+                           "jacobi_sweeps_per_update": sweeps / max(1, updates),
+                           "updates_per_step": updates / args.steps},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tnrc", choices=["tnrc", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        reference_arm(args, w)
+    else:
+        gpu_arm(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * tnrc -- tensor-network robust control on one GPU (C ABI).
+ *
+ * Computes, for the qubit chain of Eq. sysH with parasitic nearest-neighbour
+ * ZZ crosstalk, the ensemble-averaged state fidelity
+ *
+ *     F = 1/(M P) sum_{s,p} | <t_p | U^(s) | in_p> |^2          (Sec. II; F = 1 - infidelity)
+ *
+ * over M noise realisations s (Sec. II: J_b^(s) iid per bond) and P input /
+ * target state pairs, with U^(s) the second-order TEBD evolution of K
+ * piecewise-constant control slices (Sec. II, Eq. circuit) on a complex128
+ * matrix-product state truncated by SVD to bond dimension chi_max, and its
+ * exact costate gradient dF/du with respect to every control amplitude
+ * (App. A).
+ *
+ * Conventions shared by every entry point
+ *   - Sites i = 0..N-1, bonds b = 0..N-2 (bond b couples sites b, b+1).
+ *     |0> = (1,0) is the Z = +1 state.
+ *   - Controls u[K][C][N] (float64, row-major): slot 0 = x_i, slot 1 = y_i
+ *     (X / Y drives of site i), slot 2 (C = 3) = g_i, the tunable ZZ coupling
+ *     of bond (i, i+1).  A slot whose control_mask entry is 0 is not a
+ *     control: it does not enter the Hamiltonian and its gradient is 0.
+ *   - Slice k applies A(dt/2) B(dt) A(dt/2): A = the gates exp(-i tau h_b) of
+ *     all even bonds, B = of all odd bonds, with
+ *       h_b = (g_b + gfix_b + J_b) ZZ + wL (x_b X + y_b Y) (x) I + wR I (x) (x_{b+1} X + y_{b+1} Y),
+ *     wL = 1 on bond 0 else 1/2, wR = 1 on bond N-2 else 1/2.
+ *   - Truncation: after every two-site gate keep the
+ *     k = min(chi_max, #{sigma_i > max(sv_cutoff, 1e-13) sigma_1}) largest
+ *     singular values (at least one) and renormalise them to unit norm.
+ *   - MPS buffers (tnrc_mps.data): interleaved complex128, site-major, site i
+ *     stored as a row-major [D_i][2][D_{i+1}] block; bond_dims has N+1
+ *     entries with bond_dims[0] = bond_dims[N] = 1.  States are normalised on
+ *     entry.
+ *   - Ownership: every host pointer passed in is borrowed for the duration of
+ *     the call and copied; the context owns all device memory it uses.
+ *     Output host buffers are written only when the call returns TNRC_OK.
+ *   - Calls without the _dev suffix are ordered on the context's stream and
+ *     synchronous at return.  One host thread per context at a time.
+ *   - Errors: nothing aborts, traps or exits.  TNRC_E_CUDA leaves the context
+ *     unusable (destroy it); every other error leaves it usable.
+ */
+#ifndef TNRC_H
+#define TNRC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tnrc_status;
+#define TNRC_OK 0
+#define TNRC_E_INVALID (-1)   /* bad argument: NULL, size mismatch, out-of-range value  */
+#define TNRC_E_NOMEM (-2)     /* device memory for the context could not be reserved    */
+#define TNRC_E_CUDA (-3)      /* a CUDA call failed; the context is unusable             */
+#define TNRC_E_STATE (-4)     /* controls or noise not set yet                           */
+#define TNRC_E_TIMEOUT (-5)   /* reserved: no entry point waits on the device unbounded  */
+#define TNRC_E_NUMERIC (-6)   /* Jacobi SVD did not converge, or a NaN/Inf appeared      */
+
+typedef struct tnrc_ctx tnrc_ctx;
+
+/* A matrix-product state (layout above).  n_sites must equal the problem's N. */
+typedef struct {
+  int32_t n_sites;
+  const int32_t* bond_dims; /* [N+1] */
+  const double* data;       /* interleaved complex128, sum_i D_i*2*D_{i+1} values */
+} tnrc_mps;
+
+/* The problem statement (Sec. II-IV): chain, time grid, truncation, ensemble. */
+typedef struct {
+  uint32_t struct_size;          /* sizeof(tnrc_problem)                                   */
+  int32_t n_sites;               /* N >= 2                                                 */
+  int32_t n_slices;              /* K >= 1 piecewise-constant control bins                 */
+  double dt;                     /* slice length (> 0)                                     */
+  int32_t chi_max;               /* bond-dimension cap, 1 <= chi_max <= 64                  */
+  double sv_cutoff;              /* relative singular-value cutoff (>= 0; 1e-12 typical)   */
+  int32_t n_samples;             /* M >= 1 noise realisations                              */
+  int32_t n_controls;            /* C = 2 (x, y) or 3 (x, y, g)                             */
+  int32_t n_inputs;              /* P >= 1 input/target pairs                              */
+  const uint8_t* control_mask;   /* [C][N], 1 = control; NULL = all x, y (and g on bonds)  */
+  const double* g_fixed;         /* [K][N-1] fixed ZZ added on every bond, or NULL         */
+  int32_t checkpoint_every;      /* slices per backward segment; 0 = ceil(sqrt(K))         */
+} tnrc_problem;
+
+/* Per-call statistics of the last tnrc_fidelity / tnrc_fidelity_grad. */
+typedef struct {
+  int64_t updates;               /* two-site updates executed (forward, recompute, costate) */
+  int64_t jacobi_sweeps;         /* one-sided Jacobi sweeps over all updates                */
+  int32_t max_bond;              /* largest bond dimension reached                          */
+  int32_t hist_len;              /* chi_max + 1                                             */
+  int64_t bond_hist[65];         /* bond_hist[d] = forward updates that left bond dim d     */
+  double discarded_weight;       /* sum over trajectories of forward discarded weight       */
+  double last_ms;                /* device time of the last call (CUDA events), ms          */
+  double alg_flops;              /* algorithmic FP64 flops of the last evaluation: forward
+                                    and costate updates, environments, overlaps (counted
+                                    from the bond dimensions of every update; recomputation
+                                    and extra Jacobi sweeps excluded)                       */
+  double traj_ms;                /* device time of the trajectory-kernel launches since the
+                                    previous tnrc_get_stats (CUDA events on the context's
+                                    stream around each launch), ms                          */
+  int64_t traj_launches;         /* number of those launches                                */
+} tnrc_stats;
+
+/* Create a context on the current CUDA device, ordered on `cuda_stream`
+ * (a cudaStream_t, NULL = legacy default stream).  inputs[P] are the initial
+ * states |in_p>, targets[P] the targets |t_p>; both are brought to
+ * normalised canonical form (chi_max and the cutoff applied) on the device.
+ * Reserves all device memory the context will use.
+ * Errors: TNRC_E_INVALID (bad sizes or NULLs), TNRC_E_NOMEM, TNRC_E_CUDA. */
+tnrc_status tnrc_create(const tnrc_problem* problem, const tnrc_mps* inputs,
+                        const tnrc_mps* targets, void* cuda_stream, tnrc_ctx** out);
+
+/* Copy the controls u[K][C][N] (host, len = K*C*N doubles) to the device. */
+tnrc_status tnrc_set_controls(tnrc_ctx* ctx, const double* u, int64_t len);
+
+/* Draw J[M][N-1] on the device from the counter-based SplitMix64 stream of
+ * `seed`: dist 0 = uniform on [-scale, scale] (Sec. II), 1 = normal N(0, scale^2)
+ * by Box-Muller (sample s, bond b uses counter s*(N-1)+b, or 2x that and 2x+1). */
+tnrc_status tnrc_sample_noise(tnrc_ctx* ctx, uint64_t seed, int32_t dist, double scale);
+
+/* Set J[M][N-1] explicitly (host, len = M*(N-1) doubles). */
+tnrc_status tnrc_set_noise(tnrc_ctx* ctx, const double* J, int64_t len);
+
+/* Copy the current J[M][N-1] to the host (len = M*(N-1) doubles).
+ * Errors: TNRC_E_STATE if no noise was set or sampled yet. */
+tnrc_status tnrc_get_noise(tnrc_ctx* ctx, double* J, int64_t len);
+
+/* F (host scalar) and optionally per_traj[M][P] = |O_sp|^2 (host, may be NULL).
+ * Errors: TNRC_E_STATE if controls or noise are missing. */
+tnrc_status tnrc_fidelity(tnrc_ctx* ctx, double* F, double* per_traj);
+
+/* F and grad[K][C][N] = dF/du (host), with the forward states checkpointed every
+ * checkpoint_every slices and recomputed in the costate sweep (App. A). */
+tnrc_status tnrc_fidelity_grad(tnrc_ctx* ctx, double* F, double* grad);
+
+/* Overlaps O[M][P] (host, interleaved complex128) of the last evaluation. */
+tnrc_status tnrc_get_overlaps(tnrc_ctx* ctx, double* overlaps, int64_t len);
+
+/* Statistics of the last evaluation (synchronises the context's stream; the
+ * trajectory-kernel timing accumulates over calls and is reset by this call). */
+tnrc_status tnrc_get_stats(tnrc_ctx* ctx, tnrc_stats* stats);
+
+/* Device-pointer forms for autograd and serving: stream-ordered on the
+ * context's stream, asynchronous (no host synchronisation, no statistics
+ * copy).  d_u is a device array [K][C][N]; d_F a device scalar; d_grad a
+ * device array [K][C][N] (NULL for a forward-only evaluation); d_per_traj a
+ * device array [M][P] or NULL.  Errors are detected at the next synchronous
+ * call (tnrc_sync). */
+tnrc_status tnrc_set_controls_dev(tnrc_ctx* ctx, const double* d_u);
+tnrc_status tnrc_evaluate_dev(tnrc_ctx* ctx, double* d_F, double* d_grad, double* d_per_traj);
+/* Synchronise the context's stream and report any device-side error flag. */
+tnrc_status tnrc_sync(tnrc_ctx* ctx);
+
+/* Bytes of device memory tnrc_create would reserve for this problem (0 on bad input). */
+size_t tnrc_footprint(const tnrc_problem* problem);
+
+/* Release every resource of the context (NULL is accepted). */
+void tnrc_destroy(tnrc_ctx* ctx);
+
+/* Human-readable name of a status code. */
+const char* tnrc_status_string(tnrc_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNRC_H */

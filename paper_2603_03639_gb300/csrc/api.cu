@@ -1,0 +1,585 @@
+// Host runtime of the tnrc C ABI: validation, one device arena per context,
+// slot layout, launch order (noise -> gates -> trajectories -> reduction).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/tnrc.h"
+#include "tnrc_device.cuh"
+
+extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, size_t smem, cudaStream_t st);
+extern "C" size_t tnrc_traj_smem(int warps, int slab_elems);
+extern "C" cudaError_t tnrc_launch_gates(int N, int K, int C, int M, double dt, const double* u,
+                                         const unsigned char* mask, const double* gfix, const double* J,
+                                         tnrc::GateEntry* out, int* status, cudaStream_t st);
+extern "C" cudaError_t tnrc_launch_noise(unsigned long long seed, int dist, double scale, int M, int nb, double* J,
+                                         cudaStream_t st);
+extern "C" cudaError_t tnrc_launch_reduce(const double2* O, int T, double* F, double* per_traj, const double* gsp,
+                                          int X, double* grad, cudaStream_t st);
+extern "C" cudaError_t tnrc_launch_canon(const tnrc::CanonArgs* a, int nmps, cudaStream_t st);
+
+namespace {
+
+constexpr int kMaxN = 256;
+constexpr int kMaxInputDim = 128;
+
+int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+struct Plan {
+  int N, K, C, chi, M, P, T;
+  int seg, nseg;
+  int warps, slab_elems;
+  int grid;
+  std::vector<int> dcap;      // [N+1] capacity of D[i]
+  std::vector<int> site_off;  // [N]
+  tnrc::SlotLayout L;
+  int64_t scratch_elems;      // per warp
+  int64_t work_stride;        // bytes per CTA
+  int64_t env_elems;          // per CTA
+  // arena offsets (bytes)
+  int64_t off_u, off_mask, off_gfix, off_J, off_gates, off_in, off_tg, off_work, off_scratch, off_env, off_O,
+      off_gsp, off_disc, off_counters, off_status, off_wc, off_F, off_grad, off_per, off_siteoff, total;
+};
+
+bool pow2_le(int e, int chi, int& out) {
+  // min(2^e, chi) without overflow
+  if (e >= 30) {
+    out = chi;
+    return true;
+  }
+  out = std::min(1 << e, chi);
+  return true;
+}
+
+bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, bool limit_by_memory) {
+  if (!pb || pb->struct_size != sizeof(tnrc_problem)) return false;
+  const int N = pb->n_sites, K = pb->n_slices, chi = pb->chi_max;
+  if (N < 2 || N > kMaxN || K < 1 || chi < 1 || chi > tnrc::kMaxChi) return false;
+  if (!(pb->dt > 0.0) || !std::isfinite(pb->dt) || !(pb->sv_cutoff >= 0.0) || !(pb->sv_cutoff < 1.0)) return false;
+  if (pb->n_samples < 1 || pb->n_inputs < 1 || (pb->n_controls != 2 && pb->n_controls != 3)) return false;
+  if (pb->checkpoint_every < 0) return false;
+  const long long T = (long long)pb->n_samples * pb->n_inputs;
+  if (T > (1ll << 30)) return false;
+  P.N = N;
+  P.K = K;
+  P.C = pb->n_controls;
+  P.chi = chi;
+  P.M = pb->n_samples;
+  P.P = pb->n_inputs;
+  P.T = (int)T;
+  P.seg = pb->checkpoint_every > 0 ? std::min(pb->checkpoint_every, K) : (int)std::ceil(std::sqrt((double)K));
+  P.nseg = (K + P.seg - 1) / P.seg;
+  P.dcap.assign(N + 1, 1);
+  for (int i = 1; i < N; ++i) {
+    int a, b;
+    pow2_le(i, chi, a);
+    pow2_le(N - i, chi, b);
+    P.dcap[i] = std::min(a, b);
+  }
+  P.site_off.resize(N);
+  int64_t elems = 0;
+  for (int i = 0; i < N; ++i) {
+    P.site_off[i] = (int)elems;
+    elems += (int64_t)P.dcap[i] * 2 * P.dcap[i + 1];
+    elems = align_up(elems, 2);
+  }
+  P.L.N = N;
+  P.L.chi = chi;
+  P.L.lam_off = align_up((int64_t)(N + 1) * 4, 16);
+  P.L.sites_off = align_up(P.L.lam_off + (int64_t)(N - 1) * chi * 8, 256);
+  P.L.bytes = align_up(P.L.sites_off + elems * 16, 256);
+  int maxb = 0;
+  for (int par = 0; par < 2; ++par) maxb = std::max(maxb, (N - 1 - par + 1) / 2);
+  P.warps = std::max(2, std::min(tnrc::kWarps, maxb));
+  if (const char* e = getenv("TNRC_WARPS")) {
+    const int w = atoi(e);
+    if (w >= 2 && w <= tnrc::kWarps) P.warps = w;
+  }
+  P.slab_elems = std::min(1024, 4 * chi * chi);
+  const int64_t cc = (int64_t)chi * chi;
+  P.scratch_elems = 16 * cc;
+  P.env_elems = 2 * (int64_t)(N + 1) * cc;
+  P.work_stride = (int64_t)(2 + P.nseg + 3 * P.seg) * P.L.bytes;
+  const int64_t per_cta = P.work_stride + (P.scratch_elems * P.warps + P.env_elems) * 16;
+  int grid = std::min<long long>(T, n_sm);
+  if (const char* e = getenv("TNRC_GRID")) {
+    const int g = atoi(e);
+    if (g >= 1) grid = (int)std::min<long long>(T, g);
+  }
+  // fixed parts
+  int64_t off = 0;
+  auto take = [&](int64_t bytes) {
+    const int64_t o = off;
+    off = align_up(off + std::max<int64_t>(bytes, 1), 256);
+    return o;
+  };
+  const int64_t KCN = (int64_t)K * P.C * N;
+  P.off_u = take(KCN * 8);
+  P.off_mask = take((int64_t)P.C * N);
+  P.off_gfix = take((int64_t)K * (N - 1) * 8);
+  P.off_J = take((int64_t)P.M * (N - 1) * 8);
+  P.off_gates = take((int64_t)P.M * K * (N - 1) * sizeof(tnrc::GateEntry));
+  P.off_in = take((int64_t)P.P * P.L.bytes);
+  P.off_tg = take((int64_t)P.P * P.L.bytes);
+  P.off_O = take(T * 16);
+  P.off_gsp = take(T * KCN * 8);
+  P.off_disc = take(T * 8);
+  P.off_counters = take(tnrc::kNumCounters * 8);
+  P.off_status = take(16);
+  P.off_wc = take(16);
+  P.off_F = take(8);
+  P.off_grad = take(KCN * 8);
+  P.off_per = take(T * 8);
+  P.off_siteoff = take((int64_t)N * 4);
+  const int64_t fixed = off;
+  if (limit_by_memory && free_bytes > 0) {
+    const int64_t budget = (int64_t)(free_bytes * 0.85) - fixed;
+    if (budget < per_cta) return false;
+    grid = (int)std::min<int64_t>(grid, budget / per_cta);
+  }
+  P.grid = std::max(1, grid);
+  P.off_work = take((int64_t)P.grid * P.work_stride);
+  P.off_scratch = take((int64_t)P.grid * P.warps * P.scratch_elems * 16);
+  P.off_env = take((int64_t)P.grid * P.env_elems * 16);
+  P.total = off;
+  return true;
+}
+
+bool valid_mps(const tnrc_mps& m, int N) {
+  if (m.n_sites != N || !m.bond_dims || !m.data) return false;
+  if (m.bond_dims[0] != 1 || m.bond_dims[N] != 1) return false;
+  for (int i = 0; i <= N; ++i)
+    if (m.bond_dims[i] < 1 || m.bond_dims[i] > kMaxInputDim) return false;
+  return true;
+}
+
+}  // namespace
+
+struct tnrc_ctx {
+  Plan plan;
+  double dt, eps;
+  cudaStream_t stream = nullptr;
+  unsigned char* arena = nullptr;
+  bool have_u = false, have_J = false, gates_dirty = true, broken = false;
+  int last_status = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> tev;   // pairs around trajectory-kernel launches
+  size_t tev_used = 0;
+  tnrc_stats stats{};
+  int n_sm = 0;
+  template <class T>
+  T* at(int64_t off) {
+    return reinterpret_cast<T*>(arena + off);
+  }
+};
+
+namespace {
+
+tnrc_status fail_cuda(tnrc_ctx* c) {
+  if (c) c->broken = true;
+  return TNRC_E_CUDA;
+}
+
+#define CK(x)                               \
+  do {                                      \
+    if ((x) != cudaSuccess) return fail_cuda(ctx); \
+  } while (0)
+
+tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, double* dper) {
+  Plan& P = ctx->plan;
+  cudaStream_t st = ctx->stream;
+  CK(cudaEventRecord(ctx->ev0, st));
+  if (ctx->gates_dirty) {
+    CK(tnrc_launch_gates(P.N, P.K, P.C, P.M, ctx->dt, ctx->at<double>(P.off_u), ctx->at<unsigned char>(P.off_mask),
+                         ctx->at<double>(P.off_gfix), ctx->at<double>(P.off_J),
+                         ctx->at<tnrc::GateEntry>(P.off_gates), ctx->at<int>(P.off_status), st));
+    ctx->gates_dirty = false;
+  }
+  CK(cudaMemsetAsync(ctx->at<int>(P.off_wc), 0, sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->at<unsigned long long>(P.off_counters), 0, tnrc::kNumCounters * 8, st));
+  tnrc::TrajParams tp{};
+  tp.N = P.N;
+  tp.K = P.K;
+  tp.C = P.C;
+  tp.P = P.P;
+  tp.M = P.M;
+  tp.chi = P.chi;
+  tp.T = P.T;
+  tp.dt = ctx->dt;
+  tp.eps = ctx->eps;
+  tp.seg = P.seg;
+  tp.nseg = P.nseg;
+  tp.want_grad = grad ? 1 : 0;
+  tp.warps = P.warps;
+  tp.slab_elems = P.slab_elems;
+  tp.site_off = ctx->at<int>(P.off_siteoff);
+  tp.L = P.L;
+  tp.in_slots = ctx->at<unsigned char>(P.off_in);
+  tp.tg_slots = ctx->at<unsigned char>(P.off_tg);
+  tp.work = ctx->at<unsigned char>(P.off_work);
+  tp.work_stride = P.work_stride;
+  tp.warp_scratch = ctx->at<double2>(P.off_scratch);
+  tp.scratch_elems = P.scratch_elems;
+  tp.env_scratch = ctx->at<double2>(P.off_env);
+  tp.gates = ctx->at<tnrc::GateEntry>(P.off_gates);
+  tp.mask = ctx->at<unsigned char>(P.off_mask);
+  tp.O = ctx->at<double2>(P.off_O);
+  tp.gsp = ctx->at<double>(P.off_gsp);
+  tp.disc = ctx->at<double>(P.off_disc);
+  tp.counters = ctx->at<unsigned long long>(P.off_counters);
+  tp.status = ctx->at<int>(P.off_status);
+  tp.work_counter = ctx->at<int>(P.off_wc);
+  const size_t smem = tnrc_traj_smem(P.warps, P.slab_elems);
+  const bool timed = ctx->tev_used + 2 <= ctx->tev.size();
+  if (timed) CK(cudaEventRecord(ctx->tev[ctx->tev_used], st));
+  CK(tnrc_launch_traj(&tp, P.grid, smem, st));
+  if (timed) {
+    CK(cudaEventRecord(ctx->tev[ctx->tev_used + 1], st));
+    ctx->tev_used += 2;
+  }
+  const int X = P.K * P.C * P.N;
+  CK(tnrc_launch_reduce(ctx->at<double2>(P.off_O), P.T, dF ? dF : ctx->at<double>(P.off_F), dper,
+                        grad ? ctx->at<double>(P.off_gsp) : nullptr, X,
+                        grad ? (dgrad ? dgrad : ctx->at<double>(P.off_grad)) : nullptr, st));
+  CK(cudaEventRecord(ctx->ev1, st));
+  return TNRC_OK;
+}
+
+tnrc_status finish(tnrc_ctx* ctx) {
+  CK(cudaStreamSynchronize(ctx->stream));
+  int status = 0;
+  CK(cudaMemcpy(&status, ctx->at<int>(ctx->plan.off_status), sizeof(int), cudaMemcpyDeviceToHost));
+  if (status) {
+    CK(cudaMemset(ctx->at<int>(ctx->plan.off_status), 0, sizeof(int)));
+    ctx->last_status = status;
+    return TNRC_E_NUMERIC;
+  }
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) == cudaSuccess) ctx->stats.last_ms = ms;
+  return TNRC_OK;
+}
+
+tnrc_status evaluate_host(tnrc_ctx* ctx, bool grad, double* F, double* grad_out, double* per_traj) {
+  if (!ctx || !F || (grad && !grad_out)) return TNRC_E_INVALID;
+  if (ctx->broken) return TNRC_E_CUDA;
+  if (!ctx->have_u || !ctx->have_J) return TNRC_E_STATE;
+  Plan& P = ctx->plan;
+  tnrc_status s = launch_eval(ctx, grad, nullptr, nullptr, per_traj ? ctx->at<double>(P.off_per) : nullptr);
+  if (s != TNRC_OK) return s;
+  s = finish(ctx);
+  if (s != TNRC_OK) return s;
+  CK(cudaMemcpy(F, ctx->at<double>(P.off_F), 8, cudaMemcpyDeviceToHost));
+  if (grad) CK(cudaMemcpy(grad_out, ctx->at<double>(P.off_grad), (size_t)P.K * P.C * P.N * 8, cudaMemcpyDeviceToHost));
+  if (per_traj) CK(cudaMemcpy(per_traj, ctx->at<double>(P.off_per), (size_t)P.T * 8, cudaMemcpyDeviceToHost));
+  return TNRC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t tnrc_footprint(const tnrc_problem* problem) {
+  Plan P;
+  int dev = 0, n_sm = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (!make_plan(problem, n_sm, 0, P, false)) return 0;
+  return (size_t)P.total;
+}
+
+tnrc_status tnrc_create(const tnrc_problem* pb, const tnrc_mps* inputs, const tnrc_mps* targets, void* cuda_stream,
+                        tnrc_ctx** out) {
+  if (!out) return TNRC_E_INVALID;
+  *out = nullptr;
+  if (!pb || !inputs || !targets || pb->struct_size != sizeof(tnrc_problem)) return TNRC_E_INVALID;
+  {
+    Plan check;
+    if (!make_plan(pb, 1, 0, check, false)) return TNRC_E_INVALID;
+  }
+  const int N = pb->n_sites;
+  for (int p = 0; p < pb->n_inputs; ++p)
+    if (!valid_mps(inputs[p], N) || !valid_mps(targets[p], N)) return TNRC_E_INVALID;
+  if (pb->control_mask) {
+    for (int c = 0; c < pb->n_controls; ++c)
+      for (int i = 0; i < N; ++i)
+        if (pb->control_mask[c * N + i] > 1) return TNRC_E_INVALID;
+  }
+  int dev = 0, n_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TNRC_E_CUDA;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TNRC_E_CUDA;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return TNRC_E_CUDA;
+  tnrc_ctx* ctx = new (std::nothrow) tnrc_ctx();
+  if (!ctx) return TNRC_E_NOMEM;
+  if (!make_plan(pb, n_sm, 0, ctx->plan, false)) {
+    delete ctx;
+    return TNRC_E_INVALID;
+  }
+  if (!make_plan(pb, n_sm, free_b, ctx->plan, true)) {
+    delete ctx;
+    return TNRC_E_NOMEM;
+  }
+  Plan& P = ctx->plan;
+  ctx->n_sm = n_sm;
+  ctx->dt = pb->dt;
+  ctx->eps = std::max(pb->sv_cutoff, tnrc::kZeroFloor);
+  ctx->stream = (cudaStream_t)cuda_stream;
+  if (cudaMalloc(&ctx->arena, (size_t)P.total) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return TNRC_E_NOMEM;
+  }
+  auto bail = [&](tnrc_status s) {
+    tnrc_destroy(ctx);
+    return s;
+  };
+  if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess)
+    return bail(TNRC_E_CUDA);
+  ctx->tev.assign(512, nullptr);
+  for (auto& e : ctx->tev)
+    if (cudaEventCreate(&e) != cudaSuccess) return bail(TNRC_E_CUDA);
+  cudaStream_t st = ctx->stream;
+  // mask, g_fixed, site offsets, zeroed status
+  std::vector<unsigned char> mask((size_t)P.C * N, 1);
+  if (pb->control_mask) {
+    std::memcpy(mask.data(), pb->control_mask, mask.size());
+  } else if (P.C == 3) {
+    for (int i = 0; i < N; ++i) mask[2 * N + i] = (i < N - 1) ? 1 : 0;
+  }
+  if (P.C == 3) mask[2 * N + N - 1] = 0;
+  std::vector<double> gfix((size_t)P.K * (N - 1), 0.0);
+  if (pb->g_fixed) std::memcpy(gfix.data(), pb->g_fixed, gfix.size() * 8);
+  for (double v : gfix)
+    if (!std::isfinite(v)) return bail(TNRC_E_INVALID);
+  if (cudaMemcpyAsync(ctx->at<void>(P.off_mask), mask.data(), mask.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(ctx->at<void>(P.off_gfix), gfix.data(), gfix.size() * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(ctx->at<void>(P.off_siteoff), P.site_off.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaMemsetAsync(ctx->at<void>(P.off_status), 0, 16, st) != cudaSuccess ||
+      cudaMemsetAsync(ctx->at<void>(P.off_in), 0, (size_t)P.P * P.L.bytes, st) != cudaSuccess ||
+      cudaMemsetAsync(ctx->at<void>(P.off_tg), 0, (size_t)P.P * P.L.bytes, st) != cudaSuccess)
+    return bail(TNRC_E_CUDA);
+  // canonical inputs and targets
+  {
+    const int nmps = 2 * P.P;
+    std::vector<int> dims((size_t)nmps * (N + 1));
+    std::vector<long long> offs(nmps);
+    long long total = 0;
+    int dmax = P.chi;
+    for (int j = 0; j < nmps; ++j) {
+      const tnrc_mps& m = (j < P.P) ? inputs[j] : targets[j - P.P];
+      offs[j] = total;
+      for (int i = 0; i <= N; ++i) {
+        dims[(size_t)j * (N + 1) + i] = m.bond_dims[i];
+        dmax = std::max(dmax, m.bond_dims[i]);
+      }
+      for (int i = 0; i < N; ++i) total += (long long)m.bond_dims[i] * 2 * m.bond_dims[i + 1];
+    }
+    std::vector<double> raw((size_t)total * 2);
+    for (int j = 0; j < nmps; ++j) {
+      const tnrc_mps& m = (j < P.P) ? inputs[j] : targets[j - P.P];
+      long long cnt = 0;
+      for (int i = 0; i < N; ++i) cnt += (long long)m.bond_dims[i] * 2 * m.bond_dims[i + 1];
+      for (long long e = 0; e < 2 * cnt; ++e)
+        if (!std::isfinite(m.data[e])) return bail(TNRC_E_INVALID);
+      std::memcpy(raw.data() + offs[j] * 2, m.data, (size_t)cnt * 16);
+    }
+    const long long wstride = (long long)(N + 4) * 2 * dmax * dmax;
+    void *d_dims = nullptr, *d_raw = nullptr, *d_offs = nullptr, *d_work = nullptr;
+    bool ok = cudaMalloc(&d_dims, dims.size() * 4) == cudaSuccess && cudaMalloc(&d_raw, raw.size() * 8) == cudaSuccess &&
+              cudaMalloc(&d_offs, offs.size() * 8) == cudaSuccess &&
+              cudaMalloc(&d_work, (size_t)nmps * wstride * 16) == cudaSuccess;
+    if (ok) {
+      ok = cudaMemcpyAsync(d_dims, dims.data(), dims.size() * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+           cudaMemcpyAsync(d_raw, raw.data(), raw.size() * 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+           cudaMemcpyAsync(d_offs, offs.data(), offs.size() * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    }
+    if (ok) {
+      tnrc::CanonArgs a{};
+      a.N = N;
+      a.chi = P.chi;
+      a.eps = ctx->eps;
+      a.dmax = dmax;
+      a.raw_dims = (const int*)d_dims;
+      a.raw_data = (const double2*)d_raw;
+      a.raw_off = (const long long*)d_offs;
+      a.work = (double2*)d_work;
+      a.work_stride = wstride;
+      a.slots = ctx->at<unsigned char>(P.off_in);  // inputs then targets: contiguous
+      a.L = P.L;
+      a.site_off = ctx->at<int>(P.off_siteoff);
+      a.status = ctx->at<int>(P.off_status);
+      ok = (P.off_tg == P.off_in + align_up((int64_t)P.P * P.L.bytes, 256)) &&
+           tnrc_launch_canon(&a, nmps, st) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+    }
+    cudaFree(d_dims);
+    cudaFree(d_raw);
+    cudaFree(d_offs);
+    cudaFree(d_work);
+    if (!ok) {
+      cudaGetLastError();
+      return bail(TNRC_E_CUDA);
+    }
+    int status = 0;
+    if (cudaMemcpy(&status, ctx->at<int>(P.off_status), 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return bail(TNRC_E_CUDA);
+    if (status) return bail(TNRC_E_NUMERIC);
+  }
+  ctx->stats.hist_len = P.chi + 1;
+  *out = ctx;
+  return TNRC_OK;
+}
+
+tnrc_status tnrc_set_controls(tnrc_ctx* ctx, const double* u, int64_t len) {
+  if (!ctx || !u) return TNRC_E_INVALID;
+  if (ctx->broken) return TNRC_E_CUDA;
+  const Plan& P = ctx->plan;
+  if (len != (int64_t)P.K * P.C * P.N) return TNRC_E_INVALID;
+  for (int64_t i = 0; i < len; ++i)
+    if (!std::isfinite(u[i])) return TNRC_E_INVALID;
+  CK(cudaMemcpyAsync(ctx->at<void>(P.off_u), u, (size_t)len * 8, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->have_u = true;
+  ctx->gates_dirty = true;
+  return TNRC_OK;
+}
+
+tnrc_status tnrc_set_controls_dev(tnrc_ctx* ctx, const double* d_u) {
+  if (!ctx || !d_u) return TNRC_E_INVALID;
+  if (ctx->broken) return TNRC_E_CUDA;
+  const Plan& P = ctx->plan;
+  CK(cudaMemcpyAsync(ctx->at<void>(P.off_u), d_u, (size_t)P.K * P.C * P.N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  ctx->have_u = true;
+  ctx->gates_dirty = true;
+  return TNRC_OK;
+}
+
+tnrc_status tnrc_sample_noise(tnrc_ctx* ctx, uint64_t seed, int32_t dist, double scale) {
+  if (!ctx || (dist != 0 && dist != 1) || !(scale >= 0.0) || !std::isfinite(scale)) return TNRC_E_INVALID;
+  if (ctx->broken) return TNRC_E_CUDA;
+  const Plan& P = ctx->plan;
+  CK(tnrc_launch_noise(seed, dist, scale, P.M, P.N - 1, ctx->at<double>(P.off_J), ctx->stream));
+  ctx->have_J = true;
+  ctx->gates_dirty = true;
+  return TNRC_OK;
+}
+
+tnrc_status tnrc_set_noise(tnrc_ctx* ctx, const double* J, int64_t len) {
+  if (!ctx || !J) return TNRC_E_INVALID;
+  if (ctx->broken) return TNRC_E_CUDA;
+  const Plan& P = ctx->plan;
+  if (len != (int64_t)P.M * (P.N - 1)) return TNRC_E_INVALID;
+  for (int64_t i = 0; i < len; ++i)
+    if (!std::isfinite(J[i])) return TNRC_E_INVALID;
+  CK(cudaMemcpyAsync(ctx->at<void>(P.off_J), J, (size_t)len * 8, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->have_J = true;
+  ctx->gates_dirty = true;
+  return TNRC_OK;
+}
+
+tnrc_status tnrc_get_noise(tnrc_ctx* ctx, double* J, int64_t len) {
+  if (!ctx || !J) return TNRC_E_INVALID;
+  if (ctx->broken) return TNRC_E_CUDA;
+  if (!ctx->have_J) return TNRC_E_STATE;
+  const Plan& P = ctx->plan;
+  if (len != (int64_t)P.M * (P.N - 1)) return TNRC_E_INVALID;
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(J, ctx->at<void>(P.off_J), (size_t)len * 8, cudaMemcpyDeviceToHost));
+  return TNRC_OK;
+}
+
+tnrc_status tnrc_fidelity(tnrc_ctx* ctx, double* F, double* per_traj) {
+  return evaluate_host(ctx, false, F, nullptr, per_traj);
+}
+
+tnrc_status tnrc_fidelity_grad(tnrc_ctx* ctx, double* F, double* grad) {
+  return evaluate_host(ctx, true, F, grad, nullptr);
+}
+
+tnrc_status tnrc_evaluate_dev(tnrc_ctx* ctx, double* d_F, double* d_grad, double* d_per_traj) {
+  if (!ctx || !d_F) return TNRC_E_INVALID;
+  if (ctx->broken) return TNRC_E_CUDA;
+  if (!ctx->have_u || !ctx->have_J) return TNRC_E_STATE;
+  return launch_eval(ctx, d_grad != nullptr, d_F, d_grad, d_per_traj);
+}
+
+tnrc_status tnrc_sync(tnrc_ctx* ctx) {
+  if (!ctx) return TNRC_E_INVALID;
+  if (ctx->broken) return TNRC_E_CUDA;
+  return finish(ctx);
+}
+
+tnrc_status tnrc_get_overlaps(tnrc_ctx* ctx, double* overlaps, int64_t len) {
+  if (!ctx || !overlaps) return TNRC_E_INVALID;
+  if (ctx->broken) return TNRC_E_CUDA;
+  const Plan& P = ctx->plan;
+  if (len != 2 * (int64_t)P.T) return TNRC_E_INVALID;
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(overlaps, ctx->at<void>(P.off_O), (size_t)P.T * 16, cudaMemcpyDeviceToHost));
+  return TNRC_OK;
+}
+
+tnrc_status tnrc_get_stats(tnrc_ctx* ctx, tnrc_stats* stats) {
+  if (!ctx || !stats) return TNRC_E_INVALID;
+  if (ctx->broken) return TNRC_E_CUDA;
+  const Plan& P = ctx->plan;
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<unsigned long long> c(tnrc::kNumCounters);
+  CK(cudaMemcpy(c.data(), ctx->at<void>(P.off_counters), c.size() * 8, cudaMemcpyDeviceToHost));
+  std::vector<double> disc(P.T);
+  CK(cudaMemcpy(disc.data(), ctx->at<void>(P.off_disc), (size_t)P.T * 8, cudaMemcpyDeviceToHost));
+  tnrc_stats s{};
+  s.updates = (int64_t)c[0];
+  s.jacobi_sweeps = (int64_t)c[1];
+  s.max_bond = (int32_t)c[2];
+  s.hist_len = P.chi + 1;
+  for (int d = 0; d <= P.chi; ++d) s.bond_hist[d] = (int64_t)c[5 + d];
+  s.alg_flops = (double)c[3];
+  double tms = 0.0;
+  for (size_t i = 0; i + 1 < ctx->tev_used; i += 2) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->tev[i], ctx->tev[i + 1]));
+    tms += ms;
+  }
+  s.traj_ms = tms;
+  s.traj_launches = (int64_t)(ctx->tev_used / 2);
+  ctx->tev_used = 0;
+  double dw = 0.0;
+  for (double v : disc) dw += v;
+  s.discarded_weight = dw;
+  s.last_ms = ctx->stats.last_ms;
+  *stats = s;
+  return TNRC_OK;
+}
+
+void tnrc_destroy(tnrc_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  for (auto e : ctx->tev)
+    if (e) cudaEventDestroy(e);
+  delete ctx;
+}
+
+const char* tnrc_status_string(tnrc_status s) {
+  switch (s) {
+    case TNRC_OK: return "TNRC_OK";
+    case TNRC_E_INVALID: return "TNRC_E_INVALID: invalid argument";
+    case TNRC_E_NOMEM: return "TNRC_E_NOMEM: not enough device memory";
+    case TNRC_E_CUDA: return "TNRC_E_CUDA: CUDA error (context unusable)";
+    case TNRC_E_STATE: return "TNRC_E_STATE: controls or noise not set";
+    case TNRC_E_TIMEOUT: return "TNRC_E_TIMEOUT: device wait expired";
+    case TNRC_E_NUMERIC: return "TNRC_E_NUMERIC: SVD did not converge or non-finite values";
+    default: return "unknown tnrc status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,149 @@
+// Warp-level one-sided (Hestenes) Jacobi SVD in FP64 -- the truncated SVD of
+// the TEBD compression step (Sec. II: "compressed after each time step ...
+// using truncated singular-value decomposition").
+//
+// The matrix is held column-major (column j at T + j*n, n rows).  Its m
+// columns are orthogonalised by plane rotations in the round-robin (circle)
+// ordering, m/2 disjoint pairs per round, so that a whole round runs in
+// parallel: each pair gets g lanes (g a power of two, g * pairs <= 32), each
+// lane owns rows lig, lig+g, ...; the three inner products of a pair are
+// reduced over its g lanes with xor shuffles (bitwise identical in every lane,
+// so every lane takes the same decision).  After convergence column j equals
+// sigma_j y_j with y_j orthonormal: for T = M^dagger, y_j are the right
+// singular vectors of M and sigma_j its singular values.
+#pragma once
+#include "tnrc_device.cuh"
+
+namespace tnrc {
+
+__device__ __forceinline__ void rr_pair(int mp, int r, int q, int& i, int& j) {
+  if (q == 0) {
+    i = r;
+    j = mp - 1;
+  } else {
+    const int m1 = mp - 1;
+    i = (r + q) % m1;
+    j = (r - q + m1) % m1;
+  }
+}
+
+// Returns the number of sweeps (the last one made no rotation), or -kMaxSweeps
+// when the sweep limit was reached.  fro2 = squared Frobenius norm of T.
+__device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, int lane) {
+  const int mp = m + (m & 1);
+  if (mp < 2 || n < 1) return 0;
+  const int P = mp >> 1;
+  int g = 1;
+  while (g < 32 && g * 2 * P <= 32) g <<= 1;
+  const int groups = 32 / g;
+  const int lig = lane & (g - 1);
+  const unsigned gmask = (g == 32) ? 0xffffffffu : (((1u << g) - 1u) << (lane & ~(g - 1)));
+  const double thr = kJacobiZero * kJacobiZero * fro2;
+  const double tol = 2.0 * (double)(m > n ? m : n) * 2.220446049250313e-16;
+  const double tol2 = tol * tol;
+  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    int rotated = 0;
+    for (int r = 0; r < mp - 1; ++r) {
+      for (int q = lane / g; q < P; q += groups) {
+        int i, j;
+        rr_pair(mp, r, q, i, j);
+        if (i >= m || j >= m) continue;  // the padding column of an odd m is zero
+        double2* a = T + (size_t)i * n;
+        double2* b = T + (size_t)j * n;
+        double aa = 0.0, bb = 0.0;
+        double2 ab = make_double2(0.0, 0.0);
+        for (int row = lig; row < n; row += g) {
+          const double2 x = a[row], y = b[row];
+          aa = fma(x.x, x.x, fma(x.y, x.y, aa));
+          bb = fma(y.x, y.x, fma(y.y, y.y, bb));
+          cfmac(ab, x, y);
+        }
+        for (int o = g >> 1; o > 0; o >>= 1) {
+          aa += __shfl_xor_sync(gmask, aa, o);
+          bb += __shfl_xor_sync(gmask, bb, o);
+          ab.x += __shfl_xor_sync(gmask, ab.x, o);
+          ab.y += __shfl_xor_sync(gmask, ab.y, o);
+        }
+        const double ab2 = cabs2(ab);
+        if (aa > thr && bb > thr && ab2 > tol2 * aa * bb) {
+          rotated = 1;
+          // Real rotation of the pair after the phase of <a,b> is divided out:
+          // zeta = (|b|^2 - |a|^2) / (2|<a,b>|), t = tan(theta) (smaller root).
+          const double inv = rsqrt(ab2);
+          const double zeta = (bb - aa) * 0.5 * inv;
+          double t;
+          if (fabs(zeta) > 1e150)
+            t = 0.5 / zeta;
+          else
+            t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+          const double c = rsqrt(fma(t, t, 1.0));
+          const double s = c * t;
+          const double2 sp = make_double2(s * ab.x * inv, s * ab.y * inv);  // s e^{i phi}
+          // a <- c a - conj(sp) b ;  b <- c b + sp a
+          for (int row = lig; row < n; row += g) {
+            const double2 x = a[row], y = b[row];
+            double2 na = cscale(x, c);
+            na.x = fma(-sp.x, y.x, na.x);
+            na.x = fma(-sp.y, y.y, na.x);
+            na.y = fma(-sp.x, y.y, na.y);
+            na.y = fma(sp.y, y.x, na.y);
+            double2 nb = cscale(y, c);
+            cfma(nb, sp, x);
+            a[row] = na;
+            b[row] = nb;
+          }
+        }
+      }
+      __syncwarp();
+    }
+    if (!__any_sync(0xffffffffu, rotated)) return sweep + 1;
+  }
+  return -kMaxSweeps;
+}
+
+// Column norms, ranking and the truncation decision after warp_jacobi.
+// sig2[j] = |column j|^2 (j < m); perm[i] = column of rank i (i < k), ranks by
+// decreasing sigma with ties broken by the smaller index.  Returns k =
+// max(1, min(kcap, #{sigma_j > eps sigma_max})); kept2 / tot2 receive the
+// squared norms of the kept values and of all values.
+__device__ inline int warp_rank_truncate(const double2* T, int n, int m, int kcap, double eps, double* sig2,
+                                  int* perm, int lane, double& kept2, double& tot2) {
+  for (int j = lane; j < m; j += 32) {
+    const double2* c = T + (size_t)j * n;
+    double s = 0.0;
+    for (int r = 0; r < n; ++r) s = fma(c[r].x, c[r].x, fma(c[r].y, c[r].y, s));
+    sig2[j] = s;
+  }
+  __syncwarp();
+  double mx = 0.0, tot = 0.0;
+  for (int j = lane; j < m; j += 32) {
+    mx = fmax(mx, sig2[j]);
+    tot += sig2[j];
+  }
+  mx = warp_max(mx);
+  tot = warp_sum(tot);
+  const double cut2 = eps * eps * mx;
+  int cnt = 0;
+  for (int j = lane; j < m; j += 32) cnt += (sig2[j] > cut2) ? 1 : 0;
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  int k = cnt < kcap ? cnt : kcap;
+  if (k > n) k = n;  // at most n orthogonal columns of length n
+  if (k < 1) k = 1;
+  for (int j = lane; j < m; j += 32) {
+    const long long vj = __double_as_longlong(sig2[j]);
+    int rk = 0;
+    for (int i = 0; i < m; ++i) {
+      const long long vi = __double_as_longlong(sig2[i]);
+      rk += (vi > vj || (vi == vj && i < j)) ? 1 : 0;
+    }
+    if (rk < k) perm[rk] = j;
+  }
+  __syncwarp();
+  double kn = 0.0;
+  for (int i = lane; i < k; i += 32) kn += sig2[perm[i]];
+  kept2 = warp_sum(kn);
+  tot2 = tot;
+  return k;
+}
+
+}  // namespace tnrc

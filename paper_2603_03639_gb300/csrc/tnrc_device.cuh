@@ -1,0 +1,138 @@
+// Device-side data layout and helpers of the tnrc library (sm_103a).
+//
+// A "state slot" holds one MPS in right-canonical form with Schmidt values
+// (the form the TEBD two-site update of Sec. II keeps):
+//   int    D[N+1]            bond dimensions, D[0] = D[N] = 1; bond b <-> D[b+1]
+//   double lam[(N-1)*chi]    Schmidt values of bond b at lam[b*chi .. b*chi+D[b+1])
+//   double2 sites[...]       site i at site_off[i]: row-major [D[i]][2][D[i+1]]
+// Every site region is sized for the largest dimensions the site can reach,
+// Dcap_b = min(2^(b+1), 2^(N-1-b), chi), and holds the tensor packed with its
+// actual dimensions.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tnrc {
+
+constexpr int kMaxChi = 64;
+constexpr int kMaxDim = 2 * kMaxChi;        // largest theta side
+constexpr int kWarps = 8;                   // warps per trajectory CTA (upper bound)
+constexpr int kMaxSweeps = 60;              // Jacobi sweep limit
+constexpr double kZeroFloor = 1e-13;        // relative numerical-zero level of singular values
+constexpr double kJacobiZero = 5e-15;       // columns below this x ||theta||_F are left alone
+
+// device status bits (OR-ed into *status)
+constexpr int kStatusNoConverge = 1;
+constexpr int kStatusNaN = 2;
+constexpr int kStatusBadDims = 4;
+constexpr int kNumCounters = 5 + kMaxChi + 1;   // device counters of one evaluation
+
+struct SlotLayout {
+  int N, chi;
+  int64_t lam_off;    // bytes from slot start
+  int64_t sites_off;  // bytes from slot start
+  int64_t bytes;      // slot stride
+};
+
+struct GateEntry {    // one bond gate of one (sample, slice)
+  double2 G[16];      // exp(-i tau h) row-major, basis |s_b s_b+1>
+  double2 V[16];      // eigenvectors of h (columns)
+  double2 Gam[16];    // divided differences of exp(-i tau x) at the eigenvalues
+  double2 E[4];       // exp(-i tau lambda_j)
+};
+
+struct TrajParams {
+  int N, K, C, P, M, chi, T;
+  double dt, eps;              // eps = max(cutoff, kZeroFloor)
+  int seg, nseg;               // checkpoint segment length (slices) and count
+  int want_grad;
+  int warps;                   // warps per CTA
+  int slab_elems;              // complex elements of each warp's shared slab
+  const int* site_off;         // [N] complex-element offsets of the sites in a slot
+  SlotLayout L;
+  const unsigned char* in_slots;   // P canonical input slots
+  const unsigned char* tg_slots;   // P canonical target slots
+  unsigned char* work;             // per CTA: (2 + nseg + 3*seg) slots
+  int64_t work_stride;             // bytes per CTA
+  double2* warp_scratch;           // per warp: scratch_elems complex
+  int64_t scratch_elems;
+  double2* env_scratch;            // per CTA: 2*(N+1)*chi*chi complex
+  const GateEntry* gates;          // [M][K][N-1]
+  const unsigned char* mask;       // [C][N]
+  double2* O;                      // [T]
+  double* gsp;                     // [T][K*C*N] or null
+  double* disc;                    // [T]
+  unsigned long long* counters;    // see kCtrHist in traj.cu
+  int* status;
+  int* work_counter;
+};
+
+struct CanonArgs {
+  int N, chi;
+  double eps;
+  int dmax;
+  const int* raw_dims;         // [nmps][N+1]
+  const double2* raw_data;     // packed site-major
+  const long long* raw_off;    // [nmps] element offsets into raw_data
+  double2* work;               // per MPS: (N + 4) * 2 * dmax^2 complex
+  long long work_stride;       // complex elements per MPS
+  unsigned char* slots;        // nmps slots
+  SlotLayout L;
+  const int* site_off;
+  int* status;
+};
+
+// ---- small complex helpers (double2 = re, im) ----
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+// acc += a * b
+__device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void cfmac(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
+
+__device__ __forceinline__ double warp_sum(double v, unsigned mask = 0xffffffffu) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// slot accessors
+__device__ __forceinline__ int* slot_dims(unsigned char* s) { return reinterpret_cast<int*>(s); }
+__device__ __forceinline__ const int* slot_dims(const unsigned char* s) { return reinterpret_cast<const int*>(s); }
+__device__ __forceinline__ double* slot_lam(unsigned char* s, const SlotLayout& L) {
+  return reinterpret_cast<double*>(s + L.lam_off);
+}
+__device__ __forceinline__ const double* slot_lam(const unsigned char* s, const SlotLayout& L) {
+  return reinterpret_cast<const double*>(s + L.lam_off);
+}
+__device__ __forceinline__ double2* slot_sites(unsigned char* s, const SlotLayout& L) {
+  return reinterpret_cast<double2*>(s + L.sites_off);
+}
+__device__ __forceinline__ const double2* slot_sites(const unsigned char* s, const SlotLayout& L) {
+  return reinterpret_cast<const double2*>(s + L.sites_off);
+}
+
+}  // namespace tnrc

@@ -1,0 +1,569 @@
+// Persistent trajectory kernel: one CTA evaluates one trajectory (noise sample
+// s, input p) at a time and takes the next one from a device work counter.
+//
+//   forward  (Sec. II, Eq. circuit): K slices of layers A(dt/2) B(dt) A(dt/2);
+//            every two-site gate is followed by the truncated SVD; the warps of
+//            the CTA take the disjoint bonds of a layer in a fixed round-robin.
+//   overlap  (Sec. II state form): O = <t_p | a(T)> by a transfer-matrix sweep.
+//   gradient (App. A): the costate b_l = L_{l+1}^dag .. L_L^dag t is propagated
+//            backwards with the same truncated update; for every gate of layer
+//            l, dO/du += <b_l| (dG/du) G^dag |a_l> from the left/right
+//            environments of <b_l|.|a_l>; the forward states a_l are
+//            recomputed segment by segment from checkpoints every `seg` slices.
+// Each trajectory writes its own O and its own gradient row, so results do not
+// depend on which CTA ran it or on what else ran in the launch.
+#include "svd_warp.cuh"
+
+namespace tnrc {
+
+// device counters: [0] updates [1] Jacobi sweeps [2] max bond [3] algorithmic
+// FP64 flops [4] reserved [5 + d] forward updates that left bond dimension d
+constexpr int kCtrHist = 5;
+
+struct WarpCtx {
+  double2* slab;       // shared, slab_elems
+  double2* scratch;    // global, scratch_elems
+  double* sig2;        // shared, kMaxDim
+  int* perm;           // shared, kMaxDim
+  double2* small;      // shared, 48 complex (three 4x4 matrices)
+  int lane;
+  long long sweeps;
+  long long updates;
+  double disc;
+  int maxk;
+  unsigned long long alg;   // algorithmic flops counted by lane 0
+};
+
+// Algorithmic flops of one two-site update with theta of m x n (m = 2 Dl,
+// n = 2 Dr), inner bond Dc and k kept values: contraction 8 m Dc n, gate
+// 128 Dl Dr, thin SVD 4 (14 a b^2 + 8 b^3) (a = max(m, n), b = min(m, n);
+// Golub-Van Loan count, x4 for complex), split 8 m n k.
+__device__ __forceinline__ unsigned long long update_flops(int m, int n, int Dc, int k) {
+  const unsigned long long a = m > n ? m : n, b = m > n ? n : m;
+  return 8ull * m * Dc * n + 32ull * m * n + 4ull * (14ull * a * b * b + 8ull * b * b * b) + 8ull * m * n * k;
+}
+
+__device__ __forceinline__ const GateEntry& gate_at(const TrajParams& p, int s, int k, int b) {
+  return p.gates[((size_t)s * p.K + k) * (p.N - 1) + b];
+}
+
+// ---------------------------------------------------------------------------
+// Two-site update of bond b: theta = lam_{b-1} G (B_b B_{b+1}), truncated SVD,
+// B_{b+1} <- Y_k^dag, B_b <- Phi Y_k / |S_k|, lam_b <- S_k / |S_k|.
+// ---------------------------------------------------------------------------
+__device__ void two_site_update(const TrajParams& p, unsigned char* slot, int b, const GateEntry& ge,
+                                bool adjoint, bool record, bool count, WarpCtx& w) {
+  const int lane = w.lane;
+  const int chi = p.chi;
+  int* D = slot_dims(slot);
+  const int Dl = D[b], Dc = D[b + 1], Dr = D[b + 2];
+  const int m = 2 * Dl, n = 2 * Dr;
+  double2* sites = slot_sites(slot, p.L);
+  double* lam = slot_lam(slot, p.L);
+  double2* A = sites + p.site_off[b];
+  double2* Bt = sites + p.site_off[b + 1];
+  double2* T = (m * n <= p.slab_elems) ? w.slab : (w.scratch + (size_t)4 * chi * chi);
+  double2* Phi = w.scratch;
+
+  double2 g[16];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) g[r * 4 + c] = adjoint ? cconj(ge.G[c * 4 + r]) : ge.G[r * 4 + c];
+
+  // Phase 1: Phi = G (B_b B_{b+1}) and theta^dagger (column (al s1), row (s2 ga)).
+  double fro = 0.0;
+  for (int it = lane; it < Dl * Dr; it += 32) {
+    const int al = it / Dr, ga = it - al * Dr;
+    double2 acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = make_double2(0.0, 0.0);
+    const double2* a0p = A + (size_t)(al * 2) * Dc;
+    const double2* a1p = a0p + Dc;
+    for (int be = 0; be < Dc; ++be) {
+      const double2 a0 = a0p[be], a1 = a1p[be];
+      const double2 b0 = Bt[(size_t)(be * 2) * Dr + ga], b1 = Bt[(size_t)(be * 2 + 1) * Dr + ga];
+      cfma(acc[0], a0, b0);
+      cfma(acc[1], a0, b1);
+      cfma(acc[2], a1, b0);
+      cfma(acc[3], a1, b1);
+    }
+    const double ll = (b > 0) ? lam[(size_t)(b - 1) * chi + al] : 1.0;
+#pragma unroll
+    for (int s1 = 0; s1 < 2; ++s1)
+#pragma unroll
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const int row = s1 * 2 + s2;
+        double2 v = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cfma(v, g[row * 4 + q], acc[q]);
+        const size_t idx = (size_t)(al * 2 + s1) * n + s2 * Dr + ga;
+        Phi[idx] = v;
+        const double2 th = cscale(v, ll);
+        T[idx] = cconj(th);
+        fro += cabs2(th);
+      }
+  }
+  fro = warp_sum(fro);
+  __syncwarp();
+
+  // Phase 2: one-sided Jacobi on the m columns of theta^dagger.
+  const int sw = warp_jacobi(T, n, m, fro, lane);
+
+  // Phase 3: rank, truncate.
+  double kept2, tot2;
+  const int k = warp_rank_truncate(T, n, m, chi, p.eps, w.sig2, w.perm, lane, kept2, tot2);
+  if (lane == 0) {
+    if (sw < 0) atomicOr(p.status, kStatusNoConverge);
+    if (!(tot2 >= 0.0) || !(tot2 < 1e300) || !(kept2 > 0.0)) atomicOr(p.status, kStatusNaN);
+  }
+  w.sweeps += (sw < 0) ? -sw : sw;
+  w.updates += 1;
+  if (record) {
+    w.disc += (tot2 - kept2) / tot2;
+    if (k > w.maxk) w.maxk = k;
+    if (lane == 0) atomicAdd(&p.counters[kCtrHist + k], 1ull);
+  }
+  if (count) w.alg += update_flops(m, n, Dc, k);
+  const double inv_kn = rsqrt(kept2);
+
+  // Phase 4: write lam_b, B_{b+1} = Y_k^dag, B_b = Phi Y_k / |S_k|.
+  double* lamw = lam + (size_t)b * chi;
+  for (int i = lane; i < k; i += 32) lamw[i] = sqrt(w.sig2[w.perm[i]]) * inv_kn;
+  for (int it = lane; it < k * n; it += 32) {
+    const int i = it / n, r = it - i * n;
+    const int j = w.perm[i];
+    Bt[it] = cscale(cconj(T[(size_t)j * n + r]), rsqrt(w.sig2[j]));
+  }
+  for (int it = lane; it < m * k; it += 32) {
+    const int row = it / k, i = it - row * k;
+    const int j = w.perm[i];
+    const double2* ph = Phi + (size_t)row * n;
+    const double2* y = T + (size_t)j * n;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int r = 0; r < n; ++r) cfma(acc, ph[r], y[r]);
+    A[it] = cscale(acc, rsqrt(w.sig2[j]) * inv_kn);
+  }
+  __syncwarp();
+  if (lane == 0) D[b + 1] = k;
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Transfer-matrix steps of <c| . |a>.
+// Left:  Eout[b'][a'] = sum_{b,s,a} conj(c[b][s][b']) Ein[b][a] a[a][s][a']
+// Right: Eout[b][a]   = sum_{s,b',a'} conj(c[b][s][b']) Ein[b'][a'] a[a][s][a']
+// ---------------------------------------------------------------------------
+__device__ void env_left_step(const double2* Ein, int Dcl, int Dal, const double2* c, int Dcr,
+                              const double2* a, int Dar, double2* tmp, double2* Eout, int lane) {
+  const int w2 = 2 * Dar;
+  for (int it = lane; it < Dcl * w2; it += 32) {
+    const int be = it / w2, rest = it - be * w2;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int al = 0; al < Dal; ++al) cfma(acc, Ein[be * Dal + al], a[(size_t)al * w2 + rest]);
+    tmp[it] = acc;
+  }
+  __syncwarp();
+  for (int it = lane; it < Dcr * Dar; it += 32) {
+    const int bp = it / Dar, ap = it - bp * Dar;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int be = 0; be < Dcl; ++be)
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+        cfmac(acc, c[(size_t)be * 2 * Dcr + s * Dcr + bp], tmp[(size_t)be * w2 + s * Dar + ap]);
+    Eout[it] = acc;
+  }
+  __syncwarp();
+}
+
+__device__ void env_right_step(const double2* Ein, int Dcr, int Dar, const double2* c, int Dcl,
+                               const double2* a, int Dal, double2* tmp, double2* Eout, int lane) {
+  const int w2 = 2 * Dal;
+  for (int it = lane; it < Dcr * w2; it += 32) {
+    const int bp = it / w2, rest = it - bp * w2;
+    const int s = rest / Dal, al = rest - s * Dal;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int ap = 0; ap < Dar; ++ap) cfma(acc, Ein[bp * Dar + ap], a[(size_t)al * 2 * Dar + s * Dar + ap]);
+    tmp[it] = acc;
+  }
+  __syncwarp();
+  for (int it = lane; it < Dcl * Dal; it += 32) {
+    const int be = it / Dal, al = it - be * Dal;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int bp = 0; bp < Dcr; ++bp)
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+        cfmac(acc, c[(size_t)be * 2 * Dcr + s * Dcr + bp], tmp[(size_t)bp * w2 + s * Dal + al]);
+    Eout[it] = acc;
+  }
+  __syncwarp();
+}
+
+// <t|a> by one warp.
+__device__ double2 warp_overlap(const TrajParams& p, const unsigned char* tslot, const unsigned char* aslot,
+                                WarpCtx& w) {
+  const int* Dt = slot_dims(tslot);
+  const int* Da = slot_dims(aslot);
+  const double2* ts = slot_sites(tslot, p.L);
+  const double2* as = slot_sites(aslot, p.L);
+  const size_t cc = (size_t)p.chi * p.chi;
+  double2* E0 = w.scratch;
+  double2* E1 = w.scratch + cc;
+  double2* tmp = w.scratch + 2 * cc;
+  if (w.lane == 0) E0[0] = make_double2(1.0, 0.0);
+  __syncwarp();
+  for (int i = 0; i < p.N; ++i) {
+    env_left_step(E0, Dt[i], Da[i], ts + p.site_off[i], Dt[i + 1], as + p.site_off[i], Da[i + 1], tmp, E1,
+                  w.lane);
+    double2* x = E0;
+    E0 = E1;
+    E1 = x;
+  }
+  return E0[0];
+}
+
+// ---------------------------------------------------------------------------
+// Gradient of one layer: environments, mixed two-site densities, and
+// dO/du = tr(P_u Omega) with Omega = V ((Gam^T) o (e^{i tau Lam} V^dag rho V)) V^dag.
+// ---------------------------------------------------------------------------
+__device__ void layer_gradient(const TrajParams& p, const unsigned char* cslot, const unsigned char* aslot,
+                               int s, int k, int parity, double2 wO, double* gsp_row, WarpCtx& w, int warp) {
+  const int N = p.N, chi = p.chi;
+  const size_t cc = (size_t)chi * chi;
+  const int* Dc = slot_dims(cslot);
+  const int* Da = slot_dims(aslot);
+  const double2* cs = slot_sites(cslot, p.L);
+  const double2* as = slot_sites(aslot, p.L);
+  double2* Lbuf = p.env_scratch + (size_t)blockIdx.x * 2 * (N + 1) * cc;
+  double2* Rbuf = Lbuf + (size_t)(N + 1) * cc;
+  const int lane = w.lane;
+
+  // left environments L_i (sites < i) for i <= N-2, right R_i (sites >= i) for i >= 2
+  if (warp == 0) {
+    if (lane == 0) Lbuf[0] = make_double2(1.0, 0.0);
+    __syncwarp();
+    for (int i = 0; i + 1 <= N - 2; ++i) {
+      env_left_step(Lbuf + i * cc, Dc[i], Da[i], cs + p.site_off[i], Dc[i + 1], as + p.site_off[i], Da[i + 1],
+                    w.scratch, Lbuf + (i + 1) * cc, lane);
+      w.alg += 16ull * Da[i + 1] * (unsigned long long)(Dc[i] * Da[i] + Dc[i + 1] * Dc[i]);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) Rbuf[(size_t)N * cc] = make_double2(1.0, 0.0);
+    __syncwarp();
+    for (int i = N - 1; i >= 2; --i) {
+      env_right_step(Rbuf + (size_t)(i + 1) * cc, Dc[i + 1], Da[i + 1], cs + p.site_off[i], Dc[i],
+                     as + p.site_off[i], Da[i], w.scratch, Rbuf + (size_t)i * cc, lane);
+      w.alg += 16ull * Da[i] * (unsigned long long)(Dc[i + 1] * Da[i + 1] + Dc[i] * Dc[i + 1]);
+    }
+  }
+  __syncthreads();
+
+  const int nb = (N - 1 - parity + 1) / 2;
+  for (int j = warp; j < nb; j += p.warps) {
+    const int b = parity + 2 * j;
+    const int dcl = Dc[b], dcm = Dc[b + 1], dcr = Dc[b + 2];
+    const int dal = Da[b], dam = Da[b + 1], dar = Da[b + 2];
+    const double2* L = Lbuf + (size_t)b * cc;
+    const double2* R = Rbuf + (size_t)(b + 2) * cc;
+    const double2* a0 = as + p.site_off[b];
+    const double2* a1 = as + p.site_off[b + 1];
+    const double2* c0 = cs + p.site_off[b];
+    const double2* c1 = cs + p.site_off[b + 1];
+    w.alg += 8ull * dcl * (2ull * dam * dal + 4ull * dcr * dcm + 4ull * dar * dam + 4ull * dcr * dar + 16ull * dcr) +
+             2048ull;
+    double2* U1 = w.scratch;                        // [dcl][2][dam]
+    double2* U2 = U1 + 2 * cc;                      // [dcl][4][dar]
+    double2* U3 = U2 + 4 * cc;                      // [dcl][4][dcr]
+    double2* Wc = U3 + 4 * cc;                      // [dcl][4][dcr]
+    for (int it = lane; it < dcl * 2 * dam; it += 32) {
+      const int be = it / (2 * dam), rest = it - be * 2 * dam;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int al = 0; al < dal; ++al) cfma(acc, L[be * dal + al], a0[(size_t)al * 2 * dam + rest]);
+      U1[it] = acc;
+    }
+    for (int it = lane; it < dcl * 4 * dcr; it += 32) {
+      const int be = it / (4 * dcr), rest = it - be * 4 * dcr;
+      const int ss = rest / dcr, b2 = rest - ss * dcr;
+      const int s1 = ss >> 1, s2 = ss & 1;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int b1 = 0; b1 < dcm; ++b1)
+        cfma(acc, c0[(size_t)be * 2 * dcm + s1 * dcm + b1], c1[(size_t)b1 * 2 * dcr + s2 * dcr + b2]);
+      Wc[it] = acc;
+    }
+    __syncwarp();
+    for (int it = lane; it < dcl * 4 * dar; it += 32) {
+      const int be = it / (4 * dar), rest = it - be * 4 * dar;
+      const int ss = rest / dar, a2 = rest - ss * dar;
+      const int s1 = ss >> 1, s2 = ss & 1;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int a1i = 0; a1i < dam; ++a1i)
+        cfma(acc, U1[(size_t)be * 2 * dam + s1 * dam + a1i], a1[(size_t)a1i * 2 * dar + s2 * dar + a2]);
+      U2[it] = acc;
+    }
+    __syncwarp();
+    for (int it = lane; it < dcl * 4 * dcr; it += 32) {
+      const int be = it / (4 * dcr), rest = it - be * 4 * dcr;
+      const int ss = rest / dcr, b2 = rest - ss * dcr;
+      double2 acc = make_double2(0.0, 0.0);
+      const double2* u2 = U2 + (size_t)be * 4 * dar + ss * dar;
+      const double2* rr = R + (size_t)b2 * dar;
+      for (int a2 = 0; a2 < dar; ++a2) cfma(acc, u2[a2], rr[a2]);
+      U3[it] = acc;
+    }
+    __syncwarp();
+    // rho[s'][s] = sum_{be,b2} U3[be][s'][b2] conj(Wc[be][s][b2]); lane = (s', s) pair, 16 lanes x 2 halves
+    double2* rho = w.small;
+    {
+      const int o = lane & 15, half = lane >> 4;
+      const int sp = o >> 2, sq = o & 3;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int be = half; be < dcl; be += 2) {
+        const double2* u = U3 + (size_t)be * 4 * dcr + sp * dcr;
+        const double2* wv = Wc + (size_t)be * 4 * dcr + sq * dcr;
+        for (int b2 = 0; b2 < dcr; ++b2) cfmac(acc, wv[b2], u[b2]);
+      }
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
+      if (lane < 16) rho[o] = acc;
+    }
+    __syncwarp();
+    const GateEntry& ge = gate_at(p, s, k, b);
+    double2* T1 = w.small + 16;
+    double2* T2 = w.small + 32;
+    const int ri = (lane & 15) >> 2, ci = lane & 3;
+    // T1 = V^dag rho
+    if (lane < 16) {
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) cfmac(acc, ge.V[l * 4 + ri], rho[l * 4 + ci]);
+      T1[lane] = acc;
+    }
+    __syncwarp();
+    // Omega' = Gam^T o (e^{i tau lam_i} (T1 V))  -> T2
+    if (lane < 16) {
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) cfma(acc, T1[ri * 4 + l], ge.V[l * 4 + ci]);
+      acc = cmulc(acc, ge.E[ri]);
+      T2[lane] = cmul(ge.Gam[ci * 4 + ri], acc);
+    }
+    __syncwarp();
+    // T1 = V Omega'
+    if (lane < 16) {
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) cfma(acc, ge.V[ri * 4 + l], T2[l * 4 + ci]);
+      T1[lane] = acc;
+    }
+    __syncwarp();
+    // Omega = T1 V^dag -> rho (reuse)
+    if (lane < 16) {
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) cfmac(acc, ge.V[ci * 4 + l], T1[ri * 4 + l]);
+      rho[lane] = acc;
+    }
+    __syncwarp();
+    if (lane < 5) {
+      const double2* Om = rho;
+      const double wl = (b == 0) ? 1.0 : 0.5;
+      const double wr = (b + 1 == N - 1) ? 1.0 : 0.5;
+      double2 v;
+      int c = -1, site = -1;
+      if (lane == 0) {  // X on the left site
+        v = make_double2(Om[8].x + Om[13].x + Om[2].x + Om[7].x, Om[8].y + Om[13].y + Om[2].y + Om[7].y);
+        v = cscale(v, wl);
+        c = 0;
+        site = b;
+      } else if (lane == 1) {  // Y on the left site: -i Om[2+s][s] + i Om[s][2+s]
+        const double2 d = make_double2(Om[2].x + Om[7].x - Om[8].x - Om[13].x, Om[2].y + Om[7].y - Om[8].y - Om[13].y);
+        v = cscale(make_double2(-d.y, d.x), wl);
+        c = 1;
+        site = b;
+      } else if (lane == 2) {  // X on the right site
+        v = make_double2(Om[4].x + Om[1].x + Om[14].x + Om[11].x, Om[4].y + Om[1].y + Om[14].y + Om[11].y);
+        v = cscale(v, wr);
+        c = 0;
+        site = b + 1;
+      } else if (lane == 3) {  // Y on the right site: -i Om[2s+1][2s] + i Om[2s][2s+1]
+        const double2 d = make_double2(Om[1].x + Om[11].x - Om[4].x - Om[14].x, Om[1].y + Om[11].y - Om[4].y - Om[14].y);
+        v = cscale(make_double2(-d.y, d.x), wr);
+        c = 1;
+        site = b + 1;
+      } else {  // ZZ
+        v = make_double2(Om[0].x - Om[5].x - Om[10].x + Om[15].x, Om[0].y - Om[5].y - Om[10].y + Om[15].y);
+        c = (p.C == 3) ? 2 : -1;
+        site = b;
+      }
+      if (c >= 0 && p.mask[c * N + site]) {
+        // dF contribution 2 Re(conj(O) dO)
+        const double contrib = 2.0 * (wO.x * v.x + wO.y * v.y);
+        gsp_row[((size_t)k * p.C + c) * N + site] += contrib;
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+__device__ void copy_slot(const TrajParams& p, const unsigned char* src, unsigned char* dst) {
+  __syncthreads();
+  const int* Ds = slot_dims(src);
+  int* Dd = slot_dims(dst);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i <= p.N; i += nt) Dd[i] = Ds[i];
+  const double* ls = slot_lam(src, p.L);
+  double* ld = slot_lam(dst, p.L);
+  for (int b = 0; b < p.N - 1; ++b) {
+    const int d = Ds[b + 1];
+    for (int j = tid; j < d; j += nt) ld[(size_t)b * p.chi + j] = ls[(size_t)b * p.chi + j];
+  }
+  const double2* ss = slot_sites(src, p.L);
+  double2* sd = slot_sites(dst, p.L);
+  for (int i = 0; i < p.N; ++i) {
+    const int cnt = Ds[i] * 2 * Ds[i + 1];
+    const double2* a = ss + p.site_off[i];
+    double2* b = sd + p.site_off[i];
+    for (int e = tid; e < cnt; e += nt) b[e] = a[e];
+  }
+  __syncthreads();
+}
+
+__device__ void apply_layer(const TrajParams& p, unsigned char* slot, int s, int k, int parity, bool adjoint,
+                            bool record, bool count, WarpCtx& w, int warp) {
+  const int nb = (p.N - 1 - parity + 1) / 2;
+  for (int j = warp; j < nb; j += p.warps) {
+    const int b = parity + 2 * j;
+    two_site_update(p, slot, b, gate_at(p, s, k, b), adjoint, record, count, w);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kWarps * 32, 1) traj_kernel(TrajParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  __shared__ double s_disc[kWarps];
+  __shared__ int s_maxk[kWarps];
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  double2* slabs = reinterpret_cast<double2*>(smem_raw);
+  double* sig = reinterpret_cast<double*>(slabs + (size_t)p.warps * p.slab_elems);
+  int* perms = reinterpret_cast<int*>(sig + (size_t)p.warps * kMaxDim);
+  double2* smalls = reinterpret_cast<double2*>(perms + (size_t)p.warps * kMaxDim);
+
+  WarpCtx w;
+  w.slab = slabs + (size_t)warp * p.slab_elems;
+  w.scratch = p.warp_scratch + ((size_t)blockIdx.x * p.warps + warp) * p.scratch_elems;
+  w.sig2 = sig + (size_t)warp * kMaxDim;
+  w.perm = perms + (size_t)warp * kMaxDim;
+  w.small = smalls + (size_t)warp * 48;
+  w.lane = lane;
+  w.sweeps = 0;
+  w.updates = 0;
+  w.alg = 0;
+
+  unsigned char* base = p.work + (size_t)blockIdx.x * p.work_stride;
+  unsigned char* a_slot = base;
+  unsigned char* c_slot = base + p.L.bytes;
+  unsigned char* ckpt = base + 2 * p.L.bytes;
+  unsigned char* segs = ckpt + (size_t)p.nseg * p.L.bytes;
+  const int KCN = p.K * p.C * p.N;
+
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(p.work_counter, 1);
+    __syncthreads();
+    const int t = s_item;
+    __syncthreads();
+    if (t >= p.T) break;
+    const int s = t / p.P, pi = t - s * p.P;
+    w.disc = 0.0;
+    w.maxk = 0;
+    copy_slot(p, p.in_slots + (size_t)pi * p.L.bytes, a_slot);
+    // ---- forward ----
+    for (int k = 0; k < p.K; ++k) {
+      const int q = k / p.seg;
+      if (p.want_grad && (k % p.seg) == 0 && q < p.nseg - 1) copy_slot(p, a_slot, ckpt + (size_t)q * p.L.bytes);
+      for (int li = 0; li < 3; ++li) {
+        apply_layer(p, a_slot, s, k, li == 1 ? 1 : 0, false, true, true, w, warp);
+        if (p.want_grad && q == p.nseg - 1)
+          copy_slot(p, a_slot, segs + (size_t)(3 * (k - q * p.seg) + li) * p.L.bytes);
+      }
+    }
+    const unsigned char* tg = p.tg_slots + (size_t)pi * p.L.bytes;
+    __shared__ double2 s_O;
+    if (warp == 0) {
+      const double2 O = warp_overlap(p, tg, a_slot, w);
+      if (lane == 0) s_O = O;
+      for (int i = 0; i < p.N; ++i) {
+        const int* Dt = slot_dims(tg);
+        const int* Da = slot_dims(a_slot);
+        w.alg += 16ull * Da[i + 1] * (unsigned long long)(Dt[i] * Da[i] + Dt[i + 1] * Dt[i]);
+      }
+    }
+    if (lane == 0) {
+      s_disc[warp] = w.disc;
+      s_maxk[warp] = w.maxk;
+    }
+    __syncthreads();
+    const double2 O = s_O;
+    if (threadIdx.x == 0) {
+      p.O[t] = O;
+      double d = 0.0;
+      int mk = 0;
+      for (int i = 0; i < p.warps; ++i) {
+        d += s_disc[i];
+        mk = max(mk, s_maxk[i]);
+      }
+      p.disc[t] = d;
+      atomicMax(&p.counters[2], (unsigned long long)mk);
+    }
+    if (!p.want_grad) continue;
+    // ---- costate sweep ----
+    double* grow = p.gsp + (size_t)t * KCN;
+    for (int i = threadIdx.x; i < KCN; i += blockDim.x) grow[i] = 0.0;
+    copy_slot(p, tg, c_slot);
+    for (int q = p.nseg - 1; q >= 0; --q) {
+      const int k0 = q * p.seg;
+      const int k1 = min(p.K, k0 + p.seg);
+      if (q != p.nseg - 1) {
+        unsigned char* ck = ckpt + (size_t)q * p.L.bytes;
+        for (int k = k0; k < k1; ++k)
+          for (int li = 0; li < 3; ++li) {
+            apply_layer(p, ck, s, k, li == 1 ? 1 : 0, false, false, false, w, warp);
+            copy_slot(p, ck, segs + (size_t)(3 * (k - k0) + li) * p.L.bytes);
+          }
+      }
+      for (int l = 3 * (k1 - k0) - 1; l >= 0; --l) {
+        const int k = k0 + l / 3, li = l % 3;
+        const int parity = (li == 1) ? 1 : 0;
+        layer_gradient(p, c_slot, segs + (size_t)l * p.L.bytes, s, k, parity, O, grow, w, warp);
+        apply_layer(p, c_slot, s, k, parity, true, false, true, w, warp);
+      }
+    }
+  }
+  if (lane == 0) {
+    atomicAdd(&p.counters[0], (unsigned long long)w.updates);
+    atomicAdd(&p.counters[1], (unsigned long long)w.sweeps);
+    atomicAdd(&p.counters[3], w.alg);
+  }
+}
+
+}  // namespace tnrc
+
+// host-side launcher
+extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, size_t smem, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(tnrc::traj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  tnrc::traj_kernel<<<grid, p->warps * 32, smem, st>>>(*p);
+  return cudaGetLastError();
+}
+
+extern "C" size_t tnrc_traj_smem(int warps, int slab_elems) {
+  return (size_t)warps * slab_elems * sizeof(double2) + (size_t)warps * tnrc::kMaxDim * (sizeof(double) + sizeof(int)) +
+         (size_t)warps * 48 * sizeof(double2);
+}

@@ -1,0 +1,105 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every function the header declares, and rejects bad arguments before touching
+the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2603_03639_gb300 import build, tnrc
+    if not os.path.exists(tnrc.LIB_PATH):
+        build.build()
+    return tnrc.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "tnrc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tnrc_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("tnrc_create", "tnrc_set_controls", "tnrc_sample_noise", "tnrc_fidelity", "tnrc_fidelity_grad"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    from paper_2603_03639_gb300 import tnrc
+    names = declared_functions()
+    assert set(names) == set(tnrc.EXPORTS)
+    for n in names:
+        assert getattr(L, n) is not None
+
+
+def test_status_strings(L):
+    for s in (0, -1, -2, -3, -4, -5, -6):
+        assert L.tnrc_status_string(s)
+    assert b"unknown" in L.tnrc_status_string(42)
+
+
+def test_create_rejects_bad_arguments_without_a_device(L):
+    from paper_2603_03639_gb300 import tnrc
+    import synth
+    ins = synth.product_inputs(4, 1, 0)
+    base = dict(N=4, K=2, dt=0.1, chi=4, M=1, C=2)
+    bad = [dict(base, N=1), dict(base, K=0), dict(base, chi=0), dict(base, chi=65), dict(base, dt=-1.0),
+           dict(base, M=0), dict(base, C=4)]
+    dims, data = tnrc._pack(ins[0])
+    good = (tnrc.MPSDesc * 2)()
+    for x in good:
+        x.n_sites = 4
+        x.bond_dims = dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        x.data = data.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    tg = ctypes.cast(ctypes.byref(good, ctypes.sizeof(tnrc.MPSDesc)), ctypes.POINTER(tnrc.MPSDesc))
+    for kw in bad:
+        pb, keep = tnrc.make_problem(kw["N"], kw["K"], kw["dt"], kw["chi"], kw["M"], kw["C"], 1)
+        h = ctypes.c_void_p()
+        st = L.tnrc_create(ctypes.byref(pb), good, tg, None, ctypes.byref(h))
+        assert st == -1, kw
+        assert not h.value
+    # null arguments
+    pb, keep = tnrc.make_problem(4, 2, 0.1, 4, 1, 2, 1)
+    assert L.tnrc_create(None, None, None, None, None) == -1
+    h = ctypes.c_void_p()
+    assert L.tnrc_create(ctypes.byref(pb), None, None, None, ctypes.byref(h)) == -1
+    # an MPS of the wrong length or with a bad boundary bond
+    dims = np.array([1, 1, 1, 1], dtype=np.int32)
+    data = np.zeros(2 * 2 * 3)
+    d = (tnrc.MPSDesc * 2)()
+    for x in d:
+        x.n_sites = 3
+        x.bond_dims = dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        x.data = data.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert L.tnrc_create(ctypes.byref(pb), d, ctypes.cast(ctypes.byref(d, ctypes.sizeof(tnrc.MPSDesc)),
+                                                          ctypes.POINTER(tnrc.MPSDesc)), None, ctypes.byref(h)) == -1
+    # the struct size guards against a mismatched header
+    pb.struct_size = 8
+    assert L.tnrc_create(ctypes.byref(pb), d, d, None, ctypes.byref(h)) == -1
+
+
+def test_null_context_calls_are_rejected(L):
+    dp = ctypes.POINTER(ctypes.c_double)
+    x = np.zeros(4)
+    assert L.tnrc_set_controls(None, x.ctypes.data_as(dp), 4) == -1
+    assert L.tnrc_sample_noise(None, 1, 0, 0.1) == -1
+    assert L.tnrc_set_noise(None, x.ctypes.data_as(dp), 4) == -1
+    assert L.tnrc_fidelity(None, x.ctypes.data_as(dp), None) == -1
+    assert L.tnrc_fidelity_grad(None, x.ctypes.data_as(dp), x.ctypes.data_as(dp)) == -1
+    assert L.tnrc_sync(None) == -1
+    L.tnrc_destroy(None)
+
+
+def test_footprint_grows_with_the_problem(L):
+    from paper_2603_03639_gb300 import tnrc
+    small = tnrc.footprint(8, 20, 0.05, 16, 16, 2, 4)
+    big = tnrc.footprint(50, 100, 0.05, 64, 256, 3, 8)
+    assert 0 < small < big
+    assert tnrc.footprint(1, 20, 0.05, 16, 16, 2, 4) == 0

@@ -1,0 +1,173 @@
+"""GPU (C ABI) against the oracle on the same seeded inputs.
+
+Bars: |F_gpu - F_oracle| <= 1e-10, ||g_gpu - g_oracle|| <= 1e-8 ||g_oracle||
+(and per component against the largest component), per-trajectory overlaps
+to 1e-10; noise draws bit-exact (uniform) or to 1e-15 relative (normal)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import noise, robust
+from tests._util import TOL_F, TOL_O, case, gpu_context, grad_close, oracle_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def run_both(w, u=None, grad=True, g_fixed=None, checkpoint_every=0, pairs=None):
+    u, mask, J, ins, tgs = case(w, u)
+    pb = oracle_problem(w, u, mask, J, ins, tgs, g_fixed)
+    ctx = gpu_context(w, ins, tgs, mask, g_fixed, checkpoint_every)
+    ctx.set_controls(u)
+    ctx.set_noise(J)
+    if grad:
+        F, g = ctx.fidelity_grad()
+    else:
+        F = ctx.fidelity()
+        g = None
+    O = ctx.overlaps()
+    Fo, go, Oo = robust.ensemble(pb, want_grad=grad, pairs=pairs)
+    return ctx, (F, g, O), (Fo, go, Oo)
+
+
+def test_x8_fidelity_all_trajectories():
+    w = synth.WORKLOADS["x8"]
+    ctx, (F, _, O), (Fo, _, Oo) = run_both(w, grad=False)
+    assert abs(F - Fo) <= TOL_F
+    assert np.max(np.abs(O - Oo)) <= TOL_O
+    st = ctx.stats()
+    assert st["max_bond"] <= 16 and sum(st["bond_hist"]) > 0
+
+
+def test_x8_gradient_random_controls():
+    w = synth.WORKLOADS["x8"].replace(M=4)
+    _, (F, g, O), (Fo, go, Oo) = run_both(w)
+    assert abs(F - Fo) <= TOL_F
+    assert np.max(np.abs(O - Oo)) <= TOL_O
+    assert grad_close(g, go)
+
+
+def test_x8_near_solution_high_fidelity():
+    w = synth.WORKLOADS["x8"].replace(M=4, noise_scale=0.05)
+    u = synth.pi_pulse_controls(w.K, w.C, w.N, w.dt, seed=5, jitter=0.05)
+    _, (F, g, O), (Fo, go, Oo) = run_both(w, u=u)
+    assert Fo > 0.5
+    assert abs(F - Fo) <= TOL_F
+    assert grad_close(g, go)
+
+
+@pytest.mark.parametrize("N", [2, 3, 5])
+def test_short_chains_and_odd_lengths(N):
+    w = synth.WORKLOADS["x8"].replace(N=N, K=3, M=2, P=2, chi=4)
+    _, (F, g, O), (Fo, go, Oo) = run_both(w)
+    assert abs(F - Fo) <= TOL_F
+    assert grad_close(g, go)
+
+
+def test_cnot_layout_masked_g_and_fixed_zz():
+    w = synth.WORKLOADS["cnot50"].replace(N=8, K=6, chi=16, M=3, P=2)
+    rng = np.random.default_rng(3)
+    gfix = rng.normal(0, 0.2, size=(w.K, w.N - 1))
+    _, (F, g, O), (Fo, go, Oo) = run_both(w, g_fixed=gfix)
+    assert abs(F - Fo) <= TOL_F
+    assert grad_close(g, go)
+    assert np.all(g[:, 2, 1::2] == 0.0)
+
+
+def test_truncated_regime_and_large_theta():
+    # strong controls on 12 sites: bond dims reach the cap; theta up to 64 x 64
+    w = synth.WORKLOADS["ghz30"].replace(N=12, K=5, chi=32, M=1, P=1, u_sigma=1.5, dt=0.25)
+    _, (F, g, O), (Fo, go, Oo) = run_both(w)
+    assert abs(F - Fo) <= TOL_F
+    assert np.max(np.abs(O - Oo)) <= TOL_O
+    assert grad_close(g, go)
+
+
+def test_hard_truncation_chi_4():
+    w = synth.WORKLOADS["ghz30"].replace(N=10, K=4, chi=4, M=2, P=1, u_sigma=1.0, dt=0.2)
+    _, (F, g, O), (Fo, go, Oo) = run_both(w)
+    assert abs(F - Fo) <= TOL_F
+    assert grad_close(g, go)
+
+
+def test_checkpoint_segments_do_not_change_results():
+    w = synth.WORKLOADS["x8"].replace(K=7, M=2, P=2)
+    u, mask, J, ins, tgs = case(w)
+    res = []
+    for ce in (1, 3, 7, 0):
+        ctx = gpu_context(w, ins, tgs, mask, checkpoint_every=ce)
+        ctx.set_controls(u)
+        ctx.set_noise(J)
+        res.append(ctx.fidelity_grad())
+    for F, g in res[1:]:
+        assert F == res[0][0] and np.array_equal(g, res[0][1])
+
+
+def test_device_noise_matches_oracle_generator():
+    for dist, scale in ((0, 0.1), (1, 0.05)):
+        w = synth.WORKLOADS["x8"].replace(M=37, noise_dist=dist, noise_scale=scale)
+        u, mask, _, ins, tgs = case(w)
+        ctx = gpu_context(w, ins, tgs, mask)
+        ctx.sample_noise(w.seed_J, dist, scale)
+        Jg = ctx.get_noise()
+        Jo = noise.sample_J(w.seed_J, w.M, w.N, dist, scale)
+        if dist == 0:
+            assert np.array_equal(Jg, Jo)
+        else:
+            assert np.max(np.abs(Jg - Jo)) <= 1e-15 * np.max(np.abs(Jo)) * 10
+
+
+def test_repeat_calls_are_bitwise_deterministic():
+    w = synth.WORKLOADS["x8"].replace(M=4)
+    u, mask, J, ins, tgs = case(w)
+    ctx = gpu_context(w, ins, tgs, mask)
+    ctx.set_controls(u)
+    ctx.set_noise(J)
+    a = ctx.fidelity_grad()
+    b = ctx.fidelity_grad()
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+
+
+def test_state_errors_and_recovery():
+    from paper_2603_03639_gb300 import TNRCError
+    w = synth.WORKLOADS["x8"].replace(M=2, K=2)
+    u, mask, J, ins, tgs = case(w)
+    ctx = gpu_context(w, ins, tgs, mask)
+    with pytest.raises(TNRCError) as e:
+        ctx.fidelity()
+    assert e.value.status == -4
+    with pytest.raises(TNRCError):
+        ctx.set_controls(u[:1])
+    ctx.set_controls(u)
+    with pytest.raises(TNRCError):
+        ctx.set_noise(np.full_like(J, np.nan))
+    ctx.set_noise(J)
+    F = ctx.fidelity()
+    assert 0.0 <= F <= 1.0
+
+
+@pytest.mark.parametrize("name", ["x50", "cnot50", "ghz30"])
+def test_full_size_sampled_trajectories(name):
+    """Full N, K, chi in the benchmark's launch configuration, reduced to a
+    few noise samples: every overlap against the oracle, and the gradient of
+    a one-trajectory ensemble."""
+    w = synth.WORKLOADS[name].replace(M=2, P=min(2, synth.WORKLOADS[name].P))
+    u, mask, J, ins, tgs = case(w)
+    ctx = gpu_context(w, ins, tgs, mask)
+    ctx.set_controls(u)
+    ctx.set_noise(J)
+    F = ctx.fidelity()
+    O = ctx.overlaps()
+    pb = oracle_problem(w, u, mask, J, ins, tgs)
+    for s in range(w.M):
+        for p in range(w.P):
+            o, _ = robust.trajectory(pb, s, p, want_grad=False)
+            assert abs(O[s, p] - o) <= TOL_O
+    w1 = w.replace(M=1, P=1)
+    u, mask, J, ins, tgs = case(w1)
+    ctx = gpu_context(w1, ins, tgs, mask)
+    ctx.set_controls(u)
+    ctx.set_noise(J)
+    F, g = ctx.fidelity_grad()
+    Fo, go, _ = robust.ensemble(oracle_problem(w1, u, mask, J, ins, tgs))
+    assert abs(F - Fo) <= TOL_F
+    assert grad_close(g, go)
