@@ -146,6 +146,7 @@ class Context:
                  stream: Optional[int] = None):
         L = lib()
         self.N, self.K, self.C, self.M, self.P = N, K, C, M, len(inputs)
+        self.stream = int(stream or 0)
         if len(targets) != self.P:
             raise ValueError("inputs and targets differ in length")
         pb, keep = make_problem(N, K, dt, chi, M, C, self.P, cutoff, mask, g_fixed, checkpoint_every)
