@@ -57,6 +57,7 @@ typedef int32_t tnrc_status;
 #define TNRC_E_STATE (-4)     /* controls or noise not set yet                           */
 #define TNRC_E_TIMEOUT (-5)   /* reserved: no entry point waits on the device unbounded  */
 #define TNRC_E_NUMERIC (-6)   /* Jacobi SVD did not converge, or a NaN/Inf appeared      */
+#define TNRC_E_TOO_LARGE (-7) /* problem exceeds the fixed scratch of tnrc_fidelity_static */
 
 typedef struct tnrc_ctx tnrc_ctx;
 
@@ -151,6 +152,30 @@ tnrc_status tnrc_set_controls_dev(tnrc_ctx* ctx, const double* d_u);
 tnrc_status tnrc_evaluate_dev(tnrc_ctx* ctx, double* d_F, double* d_grad, double* d_per_traj);
 /* Synchronise the context's stream and report any device-side error flag. */
 tnrc_status tnrc_sync(tnrc_ctx* ctx);
+
+/* F and optionally per_traj[M][P] without allocating any device memory.
+ *
+ * For callers that cannot call cudaMalloc -- code inside a host runtime that
+ * owns every device allocation, or a process that must not grow its device
+ * footprint after start-up.  The paper has no counterpart: this is the same
+ * evaluation as tnrc_create + tnrc_set_controls + tnrc_set_noise +
+ * tnrc_fidelity (same kernels, same results), with every intermediate buffer
+ * carved from one static device array of 32 MiB compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ *   problem, inputs[P], targets[P]: as for tnrc_create (host pointers);
+ *   u[K][C][N], J[M][N-1]: host controls and noise;
+ *   cuda_stream: cudaStream_t the work is ordered on (NULL = legacy default);
+ *   F, per_traj (nullable): host outputs, written only on TNRC_OK.
+ * Synchronous at return.  Returns TNRC_E_TOO_LARGE when the problem's buffers
+ * (gate table, canonical states, one working state per CTA and its scratch)
+ * do not fit the 32 MiB array or an input bond dimension exceeds 64.  The
+ * array is shared by every call and keeps the last call's contents (each call
+ * clears what must start at zero); calls whose device work overlaps race on
+ * it and must be serialised.  The first call on a device looks up the
+ * array's device address; make it before any stream capture. */
+tnrc_status tnrc_fidelity_static(const tnrc_problem* problem, const tnrc_mps* inputs,
+                                 const tnrc_mps* targets, const double* u, const double* J,
+                                 void* cuda_stream, double* F, double* per_traj);
 
 /* Bytes of device memory tnrc_create would reserve for this problem (0 on bad input). */
 size_t tnrc_footprint(const tnrc_problem* problem);

@@ -578,6 +578,7 @@ const char* tnrc_status_string(tnrc_status s) {
     case TNRC_E_STATE: return "TNRC_E_STATE: controls or noise not set";
     case TNRC_E_TIMEOUT: return "TNRC_E_TIMEOUT: device wait expired";
     case TNRC_E_NUMERIC: return "TNRC_E_NUMERIC: SVD did not converge or non-finite values";
+    case TNRC_E_TOO_LARGE: return "TNRC_E_TOO_LARGE: problem exceeds the 32 MiB static scratch of tnrc_fidelity_static";
     default: return "unknown tnrc status";
   }
 }

@@ -14,13 +14,14 @@ LIB_PATH = os.path.join(_HERE, "lib", "libtnrc.so")
 
 TNRC_OK = 0
 STATUS_NAMES = {0: "TNRC_OK", -1: "TNRC_E_INVALID", -2: "TNRC_E_NOMEM", -3: "TNRC_E_CUDA",
-                -4: "TNRC_E_STATE", -5: "TNRC_E_TIMEOUT", -6: "TNRC_E_NUMERIC"}
+                -4: "TNRC_E_STATE", -5: "TNRC_E_TIMEOUT", -6: "TNRC_E_NUMERIC", -7: "TNRC_E_TOO_LARGE"}
 
 #: every symbol the header declares
 EXPORTS = ("tnrc_create", "tnrc_set_controls", "tnrc_sample_noise", "tnrc_set_noise", "tnrc_get_noise",
            "tnrc_fidelity",
            "tnrc_fidelity_grad", "tnrc_get_overlaps", "tnrc_get_stats", "tnrc_set_controls_dev",
-           "tnrc_evaluate_dev", "tnrc_sync", "tnrc_footprint", "tnrc_destroy", "tnrc_status_string")
+           "tnrc_evaluate_dev", "tnrc_sync", "tnrc_footprint", "tnrc_destroy", "tnrc_status_string",
+           "tnrc_fidelity_static")
 
 
 class TNRCError(RuntimeError):
@@ -78,6 +79,9 @@ def lib() -> ctypes.CDLL:
         L.tnrc_footprint.restype = ctypes.c_size_t
         L.tnrc_destroy.argtypes = [vp]
         L.tnrc_destroy.restype = None
+        L.tnrc_fidelity_static.argtypes = [ctypes.POINTER(Problem), ctypes.POINTER(MPSDesc),
+                                           ctypes.POINTER(MPSDesc), dp, dp, vp, dp, dp]
+        L.tnrc_fidelity_static.restype = i32
         L.tnrc_status_string.argtypes = [i32]
         L.tnrc_status_string.restype = ctypes.c_char_p
         for name in ("tnrc_create", "tnrc_set_controls", "tnrc_sample_noise", "tnrc_set_noise", "tnrc_get_noise",
@@ -131,6 +135,34 @@ def make_problem(N, K, dt, chi, M, C, P, cutoff=1e-12, mask=None, g_fixed=None, 
         pb.g_fixed = _dp(g)
     pb.checkpoint_every = checkpoint_every
     return pb, keep
+
+
+def _descs(states):
+    packs = [_pack(s) for s in states]
+    descs = (MPSDesc * len(packs))()
+    for d, (dims, data) in zip(descs, packs):
+        d.n_sites = len(dims) - 1
+        d.bond_dims = dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.data = _dp(data)
+    return descs, packs
+
+
+def fidelity_static(N, K, dt, chi, C, inputs, targets, u, J, cutoff=1e-12, mask=None, g_fixed=None,
+                    stream=None, per_traj=False):
+    """F (and per-trajectory |O|^2) through tnrc_fidelity_static, which
+    allocates no device memory: for callers that cannot call cudaMalloc.
+    Calls must not overlap on the GPU (they share one static array)."""
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    M, P = J.shape[0], len(inputs)
+    pb, keep = make_problem(N, K, dt, chi, M, C, P, cutoff, mask, g_fixed)
+    ins, kin = _descs(inputs)
+    tgs, ktg = _descs(targets)
+    F = np.zeros(1)
+    pt = np.zeros(M * P) if per_traj else None
+    _check(lib().tnrc_fidelity_static(ctypes.byref(pb), ins, tgs, _dp(u), _dp(J), ctypes.c_void_p(stream or 0),
+                                      _dp(F), _dp(pt) if pt is not None else None), "tnrc_fidelity_static")
+    return (F[0], pt.reshape(M, P)) if per_traj else F[0]
 
 
 def footprint(N, K, dt, chi, M, C, P, **kw) -> int:
