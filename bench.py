@@ -300,8 +300,14 @@ def main():
     ap.add_argument("--impl", default="tnrc", choices=["tnrc", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--set", action="append", default=[], metavar="KEY=VALUE",
+                    help="override a workload field (profiling cases), e.g. --set K=10 --set M=19")
     args = ap.parse_args()
     w = synth.WORKLOADS[args.workload]
+    for kv in args.set:
+        key, val = kv.split("=", 1)
+        cur = getattr(w, key)
+        w = w.replace(**{key: type(cur)(val)})
     if args.impl == "reference":
         reference_arm(args, w)
     else:
