@@ -191,12 +191,19 @@ def gpu_arm(args, w):
     F_dev = torch.zeros(1, dtype=torch.float64, device=dev)
     g_dev = torch.zeros(u.shape, dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    seed0 = w.seed_J + 1000003 * rank           # each rank draws its own noise shard
+    from paper_2603_03639_gb300.ensemble import allreduce_mean, shard_seed
+
+    def step_seed(i):
+        # step i draws a fresh global ensemble of world*M samples; this rank
+        # evaluates its slice of it
+        return shard_seed(w.seed_J + 7919 * i, rank, w.M, w.N, w.noise_dist)
 
     def step(i):
         ctx.set_controls_dev(u_dev.data_ptr())
-        ctx.sample_noise(seed0 + i, w.noise_dist, w.noise_scale)
+        ctx.sample_noise(step_seed(i), w.noise_dist, w.noise_scale)
         ctx.evaluate_dev(F_dev.data_ptr(), g_dev.data_ptr())
+        if world > 1:
+            allreduce_mean(F_dev, g_dev)           # the ensemble mean over all ranks
 
     for i in range(args.warmup):
         step(i)
@@ -245,8 +252,12 @@ def gpu_arm(args, w):
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         ctx.set_controls(u_pin)
-        ctx.sample_noise(seed0 + 7919 + i, w.noise_dist, w.noise_scale)
-        ctx.fidelity_grad()
+        ctx.sample_noise(step_seed(args.warmup + args.steps + i), w.noise_dist, w.noise_scale)
+        F_h, g_h = ctx.fidelity_grad()
+        if world > 1:
+            Ft, gt = torch.tensor([F_h], device=dev), torch.tensor(g_h, device=dev)
+            allreduce_mean(Ft, gt)
+            F_h, g_h = Ft.item(), gt.cpu().numpy()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if world > 1:
         t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
@@ -292,6 +303,95 @@ def gpu_arm(args, w):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------------------
+# serving leg
+# --------------------------------------------------------------------------
+
+def serving_problems(seed=41):
+    """Eight resident problems ("optimisers") drawn like the mixed serving
+    workload -- N in {8, 20, 30, 50}, chi in {16, 32, 64}, K, M log-uniform --
+    scaled (K in [20, 50], M in [4, 32]) so that a rate sweep ends in minutes.
+    N=8: parallel X (P=4); N=20: Heisenberg ground state from |0..0>; N=30: GHZ;
+    N=50: parallel X or CNOT by the problem's parity."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    heis = {}
+    for j in range(8):
+        N = [8, 20, 30, 50][j % 4]
+        chi = int(rng.choice([16, 32, 64]))
+        K = int(round(np.exp(rng.uniform(np.log(20), np.log(50)))))
+        M = int(round(np.exp(rng.uniform(np.log(4), np.log(32)))))
+        if N == 8:
+            w = synth.WORKLOADS["x8"].replace(chi=min(chi, 16), K=K, M=M)
+        elif N == 20:
+            w = synth.Workload("heis20", N=20, chi=chi, K=K, dt=0.05, C=3, M=M, P=1, noise_dist=0,
+                               noise_scale=0.05, seed_u=100 + j, seed_J=200 + j, seed_in=300 + j,
+                               target="heisenberg", g_bonds="all")
+        elif N == 30:
+            w = synth.WORKLOADS["ghz30"].replace(chi=chi, K=K, M=M)
+        else:
+            base = "cnot50" if (j // 4) % 2 else "x50"
+            w = synth.WORKLOADS[base].replace(chi=chi, K=K, M=M, P=2)
+        if w.target == "heisenberg":
+            if w.chi not in heis:
+                heis[w.chi] = w.states()
+            ins, tgs = heis[w.chi]
+        else:
+            ins, tgs = w.states()
+        probs.append((("p%d" % j), w, ins, tgs))
+    return probs
+
+
+def serving_run(probs, rate, n_req, max_inflight, seed):
+    from paper_2603_03639_gb300.serving import Request, Server, latency_stats
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    reqs = []
+    for i in range(n_req):
+        key, w, ins, tgs = probs[int(rng.integers(len(probs)))]
+        reqs.append(Request(key=key, N=w.N, K=w.K, dt=w.dt, chi=w.chi, M=w.M, C=w.C, inputs=ins, targets=tgs,
+                            controls=rng.normal(0, 0.5, size=(w.K, w.C, w.N)),
+                            noise_seed=int(rng.integers(1 << 40)), noise_dist=w.noise_dist,
+                            noise_scale=w.noise_scale, want_grad=bool(rng.integers(2)), mask=w.mask()))
+    srv = Server(max_inflight=max_inflight)
+    # make every problem resident first (context creation is not request latency)
+    for key, w, ins, tgs in probs:
+        warm = Request(key=key, N=w.N, K=w.K, dt=w.dt, chi=w.chi, M=w.M, C=w.C, inputs=ins, targets=tgs,
+                       controls=np.zeros((w.K, w.C, w.N)), noise_seed=1, noise_dist=w.noise_dist,
+                       noise_scale=w.noise_scale, want_grad=True, mask=w.mask())
+        srv.submit(warm)
+        srv.drain()
+    t0 = time.perf_counter()
+    for r, t in zip(reqs, arrivals):
+        now = time.perf_counter() - t0
+        if t > now:
+            time.sleep(t - now)
+        srv.submit(r)
+    srv.drain()
+    peak = srv.peak_inflight
+    srv.close()
+    st = latency_stats(reqs)
+    st["peak_inflight"] = peak
+    st["offered_rps"] = rate
+    return st, reqs
+
+
+def serving_arm(args):
+    probs = serving_problems()
+    rates = [float(x) for x in args.rates.split(",")]
+    rows = []
+    for rate in rates:
+        served, rs = serving_run(probs, rate, args.requests, 8, 1000 + int(rate * 10))
+        plain, rp = serving_run(probs, rate, args.requests, 1, 1000 + int(rate * 10))
+        same = all(a.F == b.F and (a.grad is None or np.array_equal(a.grad, b.grad)) for a, b in zip(rs, rp))
+        rows.append({"offered_rps": rate, "served": served, "plain": plain, "results_identical": same})
+    line = {"metric": "served p50/p99 latency and throughput vs plain sequential GPU calls",
+            "unit": "s, req/s", "mix": [{"key": k, "N": w.N, "chi": w.chi, "K": w.K, "M": w.M, "P": w.P,
+                                         "target": w.target} for k, w, _, _ in probs],
+            "requests_per_rate": args.requests, "max_inflight": 8, "sweep": rows, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -300,6 +400,9 @@ def main():
     ap.add_argument("--impl", default="tnrc", choices=["tnrc", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", action="store_true", help="serving rate sweep (separate JSON line)")
+    ap.add_argument("--rates", default="0.5,1,2,4")
+    ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--set", action="append", default=[], metavar="KEY=VALUE",
                     help="override a workload field (profiling cases), e.g. --set K=10 --set M=19")
     args = ap.parse_args()
@@ -308,7 +411,9 @@ def main():
         key, val = kv.split("=", 1)
         cur = getattr(w, key)
         w = w.replace(**{key: type(cur)(val)})
-    if args.impl == "reference":
+    if args.serving:
+        serving_arm(args)
+    elif args.impl == "reference":
         reference_arm(args, w)
     else:
         gpu_arm(args, w)

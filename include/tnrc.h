@@ -81,7 +81,11 @@ typedef struct {
   int32_t n_inputs;              /* P >= 1 input/target pairs                              */
   const uint8_t* control_mask;   /* [C][N], 1 = control; NULL = all x, y (and g on bonds)  */
   const double* g_fixed;         /* [K][N-1] fixed ZZ added on every bond, or NULL         */
-  int32_t checkpoint_every;      /* slices per backward segment; 0 = ceil(sqrt(K))         */
+  int32_t checkpoint_every;      /* slices per backward segment when the forward history is
+                                    recomputed; 0 = about sqrt(2K+1) layers                 */
+  int32_t warps_per_cta;         /* trajectory-kernel warps per CTA, 2..8; 0 = default      */
+  int32_t ctas_per_sm;           /* resident trajectory CTAs per SM, 1..4 with
+                                    warps_per_cta * ctas_per_sm <= 8; 0 = 1                */
 } tnrc_problem;
 
 /* Per-call statistics of the last tnrc_fidelity / tnrc_fidelity_grad. */
@@ -101,6 +105,9 @@ typedef struct {
                                     previous tnrc_get_stats (CUDA events on the context's
                                     stream around each launch), ms                          */
   int64_t traj_launches;         /* number of those launches                                */
+  int64_t restarts;              /* trajectories of the last evaluation whose forward history
+                                    did not fit their CTA's region packed and that were redone
+                                    with checkpoints (results are identical either way)     */
 } tnrc_stats;
 
 /* Create a context on the current CUDA device, ordered on `cuda_stream`

@@ -5,6 +5,11 @@ Time discretisation.  Slice k (k = 0..K-1) of length dt is the second-order
 split A(dt/2) B(dt) A(dt/2): layer A applies exp(-i tau h_b) on every even
 bond b, layer B on every odd bond, with h_b the bond Hamiltonian of
 ``oracle.gates`` built from slice k's controls.  One slice = one control bin.
+The MPS is compressed after every time step (Sec. II): the half layer A(dt/2)
+that ends slice k and the one that starts slice k+1 act on the same bonds with
+nothing in between, so they are applied as one gate (their product) followed
+by one truncated SVD.  The truncated layers are therefore
+    A_0, B_0, A_0 A_1, B_1, A_1 A_2, ..., B_{K-1}, A_{K-1}   (2K + 1 layers).
 
 Objective.  O_sp = <t_p | a_sp(T)>, F = (1/(M P)) sum_sp |O_sp|^2, the
 fidelity whose complement is the ensemble-averaged state infidelity of Sec. II.
@@ -51,10 +56,22 @@ class Problem:
 
 
 def layers(K, dt):
-    """[(k, parity, tau)] in time order."""
+    """[(k, parity, tau)] of the elementary gate layers in time order."""
     out = []
     for k in range(K):
         out += [(k, 0, dt / 2.0), (k, 1, dt), (k, 0, dt / 2.0)]
+    return out
+
+
+def merged_layers(K, dt):
+    """[(parity, [(k, tau), ...])]: the truncated layers, each the product of
+    the listed elementary layers (first in time first)."""
+    out = [(0, [(0, dt / 2.0)])]
+    for k in range(K):
+        out.append((1, [(k, dt)]))
+        if k + 1 < K:
+            out.append((0, [(k, dt / 2.0), (k + 1, dt / 2.0)]))
+    out.append((0, [(K - 1, dt / 2.0)]))
     return out
 
 
@@ -100,15 +117,18 @@ def trajectory(pb: Problem, s: int, p: int, want_grad: bool = True, stats=None):
     N = pb.N
     B, lam = _m.canonicalize(pb.inputs[p], pb.chi, pb.eps)
     T, tlam = _m.canonicalize(pb.targets[p], pb.chi, pb.eps)
-    sched = layers(pb.K, pb.dt)
+    sched = merged_layers(pb.K, pb.dt)
     gate_cache = []
     hist = [([x.copy() for x in B], [x.copy() for x in lam])] if want_grad else None
-    for (k, par, tau) in sched:
+    for (par, group) in sched:
         gl = {}
         for b in _layer_bonds(N, par):
-            G, ev, V = bond_gate(pb, s, k, b, tau)
-            gl[b] = (G, ev, V)
-            w, kk = _m.two_site_update(B, lam, b, G, pb.chi, pb.eps)
+            parts = [(k, tau) + bond_gate(pb, s, k, b, tau) for (k, tau) in group]
+            Mg = np.eye(4, dtype=np.complex128)
+            for part in parts:
+                Mg = part[2] @ Mg
+            gl[b] = (Mg, parts)
+            w, kk = _m.two_site_update(B, lam, b, Mg, pb.chi, pb.eps)
             if stats is not None:
                 stats["discarded"] += w
                 stats["dims"].append(kk)
@@ -121,21 +141,25 @@ def trajectory(pb: Problem, s: int, p: int, want_grad: bool = True, stats=None):
     dO = np.zeros((pb.K, pb.C, N), dtype=np.complex128)
     cB, clam = [x.copy() for x in T], [x.copy() for x in tlam]
     for li in range(len(sched) - 1, -1, -1):
-        k, par, tau = sched[li]
+        par, group = sched[li]
         a_after = hist[li + 1][0]
         for b in _layer_bonds(N, par):
-            G, ev, V = gate_cache[li][b]
-            slots = param_slots(pb, k, b)
-            if slots:
-                rho = _m.mixed_two_site_density(cB, a_after, b)
-                gens = _g.bond_generators(N, b)
-                for name, idx in slots:
+            Mg, parts = gate_cache[li][b]
+            rho = _m.mixed_two_site_density(cB, a_after, b)
+            gens = _g.bond_generators(N, b)
+            # gate j of the product M = G_n ... G_1:  dO/du = tr(Q_j L^dag rho L),
+            # Q_j = (dG_j/du) G_j^dag, L = G_n ... G_{j+1} (the gates after it)
+            Lt = np.eye(4, dtype=np.complex128)
+            for (k, tau, G, ev, V) in reversed(parts):
+                r = Lt.conj().T @ rho @ Lt
+                for name, idx in param_slots(pb, k, b):
                     dG = _g.dexpm_hermitian(ev, V, tau, gens[name])
                     Q = dG @ G.conj().T
-                    dO[idx] += np.trace(Q @ rho)
+                    dO[idx] += np.trace(Q @ r)
+                Lt = Lt @ G
         for b in _layer_bonds(N, par):
-            G = gate_cache[li][b][0]
-            _m.two_site_update(cB, clam, b, G.conj().T, pb.chi, pb.eps)
+            Mg = gate_cache[li][b][0]
+            _m.two_site_update(cB, clam, b, Mg.conj().T, pb.chi, pb.eps)
     return O, dO
 
 

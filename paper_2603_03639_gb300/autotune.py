@@ -1,0 +1,96 @@
+"""Launch-shape autotuner for the trajectory kernel.
+
+The kernel runs one trajectory per CTA; within a CTA the warps share the
+disjoint bonds of a TEBD layer (one warp per two-site SVD at a time).  The
+free choices are the warps per CTA (how many bonds of a layer run at once,
+and how evenly a layer's bonds divide among them) and the resident CTAs per
+SM (how many trajectories interleave on an SM; the register file holds 8 of
+this kernel's warps per SM).  The tuner times each candidate on the actual
+problem with CUDA events around the kernel and caches the fastest per shape
+bucket in a JSON file.
+
+    python -m paper_2603_03639_gb300.autotune --workload cnot50 --out tuned.json
+"""
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+CANDIDATES = [(8, 1), (6, 1), (5, 1), (4, 2), (4, 1), (3, 2), (2, 4)]
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+
+
+def shape_key(N, K, chi, M, P, C, grad=True):
+    """Shape bucket: N and C exactly; K, M*P and chi by powers of two."""
+    b = lambda x: 1 << int(np.ceil(np.log2(max(1, x))))  # noqa: E731
+    return "N%d-C%d-K%d-T%d-chi%d-%s" % (N, C, b(K), b(M * P), b(chi), "grad" if grad else "fid")
+
+
+def load(path=None):
+    path = path or os.environ.get("TNRC_AUTOTUNE_CACHE", DEFAULT_CACHE)
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def lookup(N, K, chi, M, P, C, grad=True, path=None):
+    """(warps_per_cta, ctas_per_sm) cached for this shape, or (0, 0)."""
+    e = load(path).get(shape_key(N, K, chi, M, P, C, grad))
+    return (int(e["warps"]), int(e["ctas_per_sm"])) if e else (0, 0)
+
+
+def tune(N, K, dt, chi, M, C, inputs, targets, u, noise, mask=None, grad=True, candidates=CANDIDATES, reps=1,
+         stream=None):
+    """Time every candidate; returns (best (warps, ctas), {candidate: ms})."""
+    from .tnrc import Context
+    seed, dist, scale = noise
+    nb = max((N - 1 + 1) // 2, 1)
+    times = {}
+    for w, c in candidates:
+        if w * c > 8 or w > max(2, nb):
+            continue
+        with Context(N, K, dt, chi, M, C, inputs, targets, mask=mask, stream=stream, warps=w, ctas_per_sm=c) as ctx:
+            ctx.set_controls(u)
+            ctx.sample_noise(seed, dist, scale)
+            (ctx.fidelity_grad if grad else ctx.fidelity)()          # warm-up
+            ctx.stats()
+            for _ in range(reps):
+                (ctx.fidelity_grad if grad else ctx.fidelity)()
+            st = ctx.stats()
+            times[(w, c)] = st["traj_ms"] / max(1, st["traj_launches"])
+    best = min(times, key=times.get)
+    return best, times
+
+
+def main():
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="cnot50", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--set", action="append", default=[], metavar="KEY=VALUE")
+    ap.add_argument("--out", default=DEFAULT_CACHE)
+    ap.add_argument("--fidelity-only", action="store_true")
+    args = ap.parse_args()
+    w = synth.WORKLOADS[args.workload]
+    for kv in args.set:
+        key, val = kv.split("=", 1)
+        w = w.replace(**{key: type(getattr(w, key))(val)})
+    ins, tgs = w.states()
+    grad = not args.fidelity_only
+    best, times = tune(w.N, w.K, w.dt, w.chi, w.M, w.C, ins, tgs, w.controls(),
+                       (w.seed_J, w.noise_dist, w.noise_scale), mask=w.mask(), grad=grad)
+    cache = load(args.out)
+    key = shape_key(w.N, w.K, w.chi, w.M, w.P, w.C, grad)
+    cache[key] = {"warps": best[0], "ctas_per_sm": best[1], "workload": w.name,
+                  "ms": {"%dx%d" % k: round(v, 3) for k, v in times.items()}}
+    with open(args.out, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    print(json.dumps({"key": key, "best": best, "ms": {"%dx%d" % k: v for k, v in times.items()}}))
+
+
+if __name__ == "__main__":
+    main()

@@ -16,7 +16,7 @@ extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, siz
 extern "C" size_t tnrc_traj_smem(int warps, int slab_elems);
 extern "C" cudaError_t tnrc_launch_gates(int N, int K, int C, int M, double dt, const double* u,
                                          const unsigned char* mask, const double* gfix, const double* J,
-                                         tnrc::GateEntry* out, int* status, cudaStream_t st);
+                                         tnrc::GateEntry* out, double2* merged, int* status, cudaStream_t st);
 extern "C" cudaError_t tnrc_launch_noise(unsigned long long seed, int dist, double scale, int M, int nb, double* J,
                                          cudaStream_t st);
 extern "C" cudaError_t tnrc_launch_reduce(const double2* O, int T, double* F, double* per_traj, const double* gsp,
@@ -30,6 +30,37 @@ constexpr int kMaxInputDim = 128;
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+// Capacities min(2^i, 2^(N-i), cap), site offsets and byte layout of a slot.
+struct Layout {
+  std::vector<int> dcap;      // [N+1] capacity of D[i]
+  std::vector<int> site_off;  // [N]
+  tnrc::SlotLayout L;
+  int seg = 1, nseg = 1;
+};
+
+Layout make_layout(int N, int cap) {
+  Layout Y;
+  Y.dcap.assign(N + 1, 1);
+  for (int i = 1; i < N; ++i) {
+    const int a = i >= 30 ? cap : std::min(1 << i, cap);
+    const int b = (N - i) >= 30 ? cap : std::min(1 << (N - i), cap);
+    Y.dcap[i] = std::min(a, b);
+  }
+  Y.site_off.resize(N);
+  int64_t elems = 0;
+  for (int i = 0; i < N; ++i) {
+    Y.site_off[i] = (int)elems;
+    elems += (int64_t)Y.dcap[i] * 2 * Y.dcap[i + 1];
+    elems = align_up(elems, 2);
+  }
+  Y.L.N = N;
+  Y.L.chi = cap;
+  Y.L.lam_off = align_up((int64_t)(N + 1) * 4, 16);
+  Y.L.sites_off = align_up(Y.L.lam_off + (int64_t)(N - 1) * cap * 8, 256);
+  Y.L.bytes = align_up(Y.L.sites_off + elems * 16, 256);
+  return Y;
+}
+
 struct Plan {
   int N, K, C, chi, M, P, T;
   int seg, nseg;
@@ -42,19 +73,10 @@ struct Plan {
   int64_t work_stride;        // bytes per CTA
   int64_t env_elems;          // per CTA
   // arena offsets (bytes)
+  int64_t off_merged;
   int64_t off_u, off_mask, off_gfix, off_J, off_gates, off_in, off_tg, off_work, off_scratch, off_env, off_O,
-      off_gsp, off_disc, off_counters, off_status, off_wc, off_F, off_grad, off_per, off_siteoff, total;
+      off_gsp, off_disc, off_counters, off_status, off_wc, off_F, off_grad, off_per, off_siteoff, off_dcap, total;
 };
-
-bool pow2_le(int e, int chi, int& out) {
-  // min(2^e, chi) without overflow
-  if (e >= 30) {
-    out = chi;
-    return true;
-  }
-  out = std::min(1 << e, chi);
-  return true;
-}
 
 bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, bool limit_by_memory) {
   if (!pb || pb->struct_size != sizeof(tnrc_problem)) return false;
@@ -72,41 +94,35 @@ bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, boo
   P.M = pb->n_samples;
   P.P = pb->n_inputs;
   P.T = (int)T;
-  P.seg = pb->checkpoint_every > 0 ? std::min(pb->checkpoint_every, K) : (int)std::ceil(std::sqrt((double)K));
-  P.nseg = (K + P.seg - 1) / P.seg;
-  P.dcap.assign(N + 1, 1);
-  for (int i = 1; i < N; ++i) {
-    int a, b;
-    pow2_le(i, chi, a);
-    pow2_le(N - i, chi, b);
-    P.dcap[i] = std::min(a, b);
+  // checkpoint segments in truncated layers (2K+1 of them; 2 per slice)
+  const int L = 2 * K + 1;
+  P.seg = pb->checkpoint_every > 0 ? std::min(2 * pb->checkpoint_every, L) : (int)std::ceil(std::sqrt((double)L));
+  P.nseg = (L + P.seg - 1) / P.seg;
+  {
+    Layout Y = make_layout(N, chi);
+    P.dcap = Y.dcap;
+    P.site_off = Y.site_off;
+    P.L = Y.L;
   }
-  P.site_off.resize(N);
-  int64_t elems = 0;
-  for (int i = 0; i < N; ++i) {
-    P.site_off[i] = (int)elems;
-    elems += (int64_t)P.dcap[i] * 2 * P.dcap[i + 1];
-    elems = align_up(elems, 2);
-  }
-  P.L.N = N;
-  P.L.chi = chi;
-  P.L.lam_off = align_up((int64_t)(N + 1) * 4, 16);
-  P.L.sites_off = align_up(P.L.lam_off + (int64_t)(N - 1) * chi * 8, 256);
-  P.L.bytes = align_up(P.L.sites_off + elems * 16, 256);
   int maxb = 0;
   for (int par = 0; par < 2; ++par) maxb = std::max(maxb, (N - 1 - par + 1) / 2);
   P.warps = std::max(2, std::min(tnrc::kWarps, maxb));
+  if (pb->warps_per_cta < 0 || pb->warps_per_cta == 1 || pb->warps_per_cta > tnrc::kWarps) return false;
+  if (pb->ctas_per_sm < 0 || pb->ctas_per_sm > 4) return false;
+  if (pb->warps_per_cta > 0) P.warps = pb->warps_per_cta;
   if (const char* e = getenv("TNRC_WARPS")) {
     const int w = atoi(e);
     if (w >= 2 && w <= tnrc::kWarps) P.warps = w;
   }
+  // the register file holds 8 warps of this kernel per SM
+  const int ctas_per_sm = std::max(1, std::min(pb->ctas_per_sm > 0 ? pb->ctas_per_sm : 1, tnrc::kWarps / P.warps));
   P.slab_elems = std::min(1024, 4 * chi * chi);
   const int64_t cc = (int64_t)chi * chi;
   P.scratch_elems = 16 * cc;
   P.env_elems = 2 * (int64_t)(N + 1) * cc;
-  P.work_stride = (int64_t)(2 + P.nseg + 3 * P.seg) * P.L.bytes;
+  P.work_stride = (int64_t)(2 + P.nseg + P.seg) * P.L.bytes;
   const int64_t per_cta = P.work_stride + (P.scratch_elems * P.warps + P.env_elems) * 16;
-  int grid = std::min<long long>(T, n_sm);
+  int grid = (int)std::min<long long>(T, (long long)n_sm * ctas_per_sm);
   if (const char* e = getenv("TNRC_GRID")) {
     const int g = atoi(e);
     if (g >= 1) grid = (int)std::min<long long>(T, g);
@@ -124,6 +140,7 @@ bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, boo
   P.off_gfix = take((int64_t)K * (N - 1) * 8);
   P.off_J = take((int64_t)P.M * (N - 1) * 8);
   P.off_gates = take((int64_t)P.M * K * (N - 1) * sizeof(tnrc::GateEntry));
+  P.off_merged = take((int64_t)P.M * std::max(K - 1, 1) * (N - 1) * 16 * 16);
   P.off_in = take((int64_t)P.P * P.L.bytes);
   P.off_tg = take((int64_t)P.P * P.L.bytes);
   P.off_O = take(T * 16);
@@ -136,6 +153,8 @@ bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, boo
   P.off_grad = take(KCN * 8);
   P.off_per = take(T * 8);
   P.off_siteoff = take((int64_t)N * 4);
+  P.off_dcap = take((int64_t)(N + 1) * 4);
+
   const int64_t fixed = off;
   if (limit_by_memory && free_bytes > 0) {
     const int64_t budget = (int64_t)(free_bytes * 0.85) - fixed;
@@ -170,6 +189,10 @@ struct tnrc_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> tev;   // pairs around trajectory-kernel launches
   size_t tev_used = 0;
+  // the forward history of the costate sweep is kept packed at the actual bond
+  // dimensions in each CTA's work region when it fits (else checkpoints)
+  int packed_history = 1;
+  long long history_cap = (long long)1 << 62;
   tnrc_stats stats{};
   int n_sm = 0;
   template <class T>
@@ -197,7 +220,8 @@ tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, dou
   if (ctx->gates_dirty) {
     CK(tnrc_launch_gates(P.N, P.K, P.C, P.M, ctx->dt, ctx->at<double>(P.off_u), ctx->at<unsigned char>(P.off_mask),
                          ctx->at<double>(P.off_gfix), ctx->at<double>(P.off_J),
-                         ctx->at<tnrc::GateEntry>(P.off_gates), ctx->at<int>(P.off_status), st));
+                         ctx->at<tnrc::GateEntry>(P.off_gates), ctx->at<double2>(P.off_merged),
+                         ctx->at<int>(P.off_status), st));
     ctx->gates_dirty = false;
   }
   CK(cudaMemsetAsync(ctx->at<int>(P.off_wc), 0, sizeof(int), st));
@@ -212,13 +236,16 @@ tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, dou
   tp.T = P.T;
   tp.dt = ctx->dt;
   tp.eps = ctx->eps;
-  tp.seg = P.seg;
-  tp.nseg = P.nseg;
   tp.want_grad = grad ? 1 : 0;
   tp.warps = P.warps;
   tp.slab_elems = P.slab_elems;
-  tp.site_off = ctx->at<int>(P.off_siteoff);
-  tp.L = P.L;
+  tp.full.L = P.L;
+  tp.full.site_off = ctx->at<int>(P.off_siteoff);
+  tp.full.dcap = ctx->at<int>(P.off_dcap);
+  tp.full.seg = P.seg;
+  tp.full.nseg = P.nseg;
+  tp.packed_history = ctx->packed_history;
+  tp.history_cap = ctx->history_cap;
   tp.in_slots = ctx->at<unsigned char>(P.off_in);
   tp.tg_slots = ctx->at<unsigned char>(P.off_tg);
   tp.work = ctx->at<unsigned char>(P.off_work);
@@ -227,6 +254,7 @@ tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, dou
   tp.scratch_elems = P.scratch_elems;
   tp.env_scratch = ctx->at<double2>(P.off_env);
   tp.gates = ctx->at<tnrc::GateEntry>(P.off_gates);
+  tp.merged = ctx->at<double2>(P.off_merged);
   tp.mask = ctx->at<unsigned char>(P.off_mask);
   tp.O = ctx->at<double2>(P.off_O);
   tp.gsp = ctx->at<double>(P.off_gsp);
@@ -359,6 +387,8 @@ tnrc_status tnrc_create(const tnrc_problem* pb, const tnrc_mps* inputs, const tn
       cudaMemcpyAsync(ctx->at<void>(P.off_gfix), gfix.data(), gfix.size() * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(ctx->at<void>(P.off_siteoff), P.site_off.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
+      cudaMemcpyAsync(ctx->at<void>(P.off_dcap), P.dcap.data(), (size_t)(N + 1) * 4, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
       cudaMemsetAsync(ctx->at<void>(P.off_status), 0, 16, st) != cudaSuccess ||
       cudaMemsetAsync(ctx->at<void>(P.off_in), 0, (size_t)P.P * P.L.bytes, st) != cudaSuccess ||
       cudaMemsetAsync(ctx->at<void>(P.off_tg), 0, (size_t)P.P * P.L.bytes, st) != cudaSuccess)
@@ -430,6 +460,8 @@ tnrc_status tnrc_create(const tnrc_problem* pb, const tnrc_mps* inputs, const tn
     if (status) return bail(TNRC_E_NUMERIC);
   }
   ctx->stats.hist_len = P.chi + 1;
+  if (const char* e = getenv("TNRC_PACKED_HISTORY")) ctx->packed_history = atoi(e) != 0;
+  if (const char* e = getenv("TNRC_HISTORY_CAP")) ctx->history_cap = std::max(0ll, atoll(e));
   *out = ctx;
   return TNRC_OK;
 }
@@ -540,6 +572,7 @@ tnrc_status tnrc_get_stats(tnrc_ctx* ctx, tnrc_stats* stats) {
   s.hist_len = P.chi + 1;
   for (int d = 0; d <= P.chi; ++d) s.bond_hist[d] = (int64_t)c[5 + d];
   s.alg_flops = (double)c[3];
+  s.restarts = (int64_t)c[4];
   double tms = 0.0;
   for (size_t i = 0; i + 1 < ctx->tev_used; i += 2) {
     float ms = 0.f;

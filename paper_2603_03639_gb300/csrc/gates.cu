@@ -172,6 +172,29 @@ __global__ void gate_kernel(GateArgs a) {
   for (int j = 0; j < 4; ++j) ge.E[j] = E[j];
 }
 
+// Merged half-step gates of the even bonds: Gm[s][k][b] = G[s][k+1][b] G[s][k][b]
+// (k = 0..K-2), the A(dt/2) that ends slice k followed by the one that starts
+// slice k+1, applied as one gate before one truncation.
+__global__ void merge_kernel(int N, int K, int M, const GateEntry* g, double2* gm) {
+  const int nb = N - 1;
+  const int ne = (nb + 1) / 2;  // even bonds
+  const long long total = (long long)M * (K - 1) * ne * 16;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int e = (int)(idx & 15);
+  const long long rest = idx >> 4;
+  const int b = 2 * (int)(rest % ne);
+  const int k = (int)((rest / ne) % (K - 1));
+  const int s = (int)(rest / ((long long)ne * (K - 1)));
+  const GateEntry& g1 = g[((size_t)s * K + k) * nb + b];
+  const GateEntry& g2 = g[((size_t)s * K + k + 1) * nb + b];
+  const int r = e >> 2, c = e & 3;
+  double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) cfma(acc, g2.G[r * 4 + j], g1.G[j * 4 + c]);
+  gm[(((size_t)s * (K - 1) + k) * nb + b) * 16 + e] = acc;
+}
+
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long i) {
   unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -224,12 +247,16 @@ __global__ void reduce_grad_kernel(const double* gsp, int T, int X, double* grad
 
 extern "C" cudaError_t tnrc_launch_gates(int N, int K, int C, int M, double dt, const double* u,
                                          const unsigned char* mask, const double* gfix, const double* J,
-                                         tnrc::GateEntry* out, int* status, cudaStream_t st) {
+                                         tnrc::GateEntry* out, double2* merged, int* status, cudaStream_t st) {
   tnrc::GateArgs a{N, K, C, M, dt, u, mask, gfix, J, out, status};
   const long long total = (long long)M * K * (N - 1);
   const int threads = 128;
   const long long blocks = (total + threads - 1) / threads;
   tnrc::gate_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);
+  if (K > 1) {
+    const long long tm = (long long)M * (K - 1) * (N / 2) * 16;
+    tnrc::merge_kernel<<<(unsigned)((tm + 255) / 256), 256, 0, st>>>(N, K, M, out, merged);
+  }
   return cudaGetLastError();
 }
 

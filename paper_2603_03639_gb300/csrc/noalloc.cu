@@ -32,7 +32,7 @@ extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, siz
 extern "C" size_t tnrc_traj_smem(int warps, int slab_elems);
 extern "C" cudaError_t tnrc_launch_gates(int N, int K, int C, int M, double dt, const double* u,
                                          const unsigned char* mask, const double* gfix, const double* J,
-                                         tnrc::GateEntry* out, int* status, cudaStream_t st);
+                                         tnrc::GateEntry* out, double2* merged, int* status, cudaStream_t st);
 extern "C" cudaError_t tnrc_launch_reduce(const double2* O, int T, double* F, double* per_traj, const double* gsp,
                                           int X, double* grad, cudaStream_t st);
 extern "C" cudaError_t tnrc_launch_canon(const tnrc::CanonArgs* a, int nmps, cudaStream_t st);
@@ -139,10 +139,12 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   };
   const int64_t o_mask = take((int64_t)C * N), o_gfix = take((int64_t)K * (N - 1) * 8), o_u = take(KCN * 8),
                 o_J = take((int64_t)M * (N - 1) * 8), o_site = take((int64_t)N * 4),
+                o_dcap = take((int64_t)(N + 1) * 4),
                 o_rdims = take((int64_t)rdims.size() * 4), o_roffs = take((int64_t)roffs.size() * 8),
                 o_raw = take(rtotal * 16), o_cwork = take((int64_t)2 * P * cwork * 16),
                 o_slots = take((int64_t)2 * P * L.bytes),
-                o_gates = take((int64_t)M * K * (N - 1) * sizeof(tnrc::GateEntry)), o_O = take(T * 16),
+                o_gates = take((int64_t)M * K * (N - 1) * sizeof(tnrc::GateEntry)),
+                o_merged = take((int64_t)M * std::max(K - 1, 1) * (N - 1) * 256), o_O = take(T * 16),
                 o_disc = take(T * 8), o_per = take(T * 8), o_small = take(4096);
   int maxb = 0;
   for (int par = 0; par < 2; ++par) maxb = std::max(maxb, (N - 1 - par + 1) / 2);
@@ -193,6 +195,7 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
             cudaMemcpyAsync(base + o_u, u, KCN * 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(base + o_J, J, (size_t)M * (N - 1) * 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(base + o_site, site_off.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+            cudaMemcpyAsync(base + o_dcap, dcap.data(), (size_t)(N + 1) * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(base + o_rdims, rdims.data(), rdims.size() * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(base + o_roffs, roffs.data(), roffs.size() * 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(base + o_raw, raw.data(), raw.size() * 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
@@ -225,7 +228,8 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   // ---- gates ----
   if (tnrc_launch_gates(N, K, C, M, pb->dt, reinterpret_cast<const double*>(base + o_u), base + o_mask,
                         reinterpret_cast<const double*>(base + o_gfix), reinterpret_cast<const double*>(base + o_J),
-                        reinterpret_cast<tnrc::GateEntry*>(base + o_gates), status, st) != cudaSuccess)
+                        reinterpret_cast<tnrc::GateEntry*>(base + o_gates),
+                        reinterpret_cast<double2*>(base + o_merged), status, st) != cudaSuccess)
     return TNRC_E_CUDA;
   // ---- trajectories (forward and overlap only) ----
   tnrc::TrajParams tp{};
@@ -238,13 +242,16 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   tp.T = (int)T;
   tp.dt = pb->dt;
   tp.eps = eps;
-  tp.seg = K;
-  tp.nseg = 1;
   tp.want_grad = 0;
   tp.warps = warps;
   tp.slab_elems = slab;
-  tp.site_off = reinterpret_cast<const int*>(base + o_site);
-  tp.L = L;
+  tp.full.L = L;
+  tp.full.site_off = reinterpret_cast<const int*>(base + o_site);
+  tp.full.dcap = reinterpret_cast<const int*>(base + o_dcap);
+  tp.full.seg = 2 * K + 1;
+  tp.full.nseg = 1;
+  tp.packed_history = 0;
+  tp.history_cap = 0;
   tp.in_slots = base + o_slots;
   tp.tg_slots = base + o_slots + (size_t)P * L.bytes;
   tp.work = base + o_work;
@@ -253,6 +260,7 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   tp.scratch_elems = scratch_elems;
   tp.env_scratch = reinterpret_cast<double2*>(base + o_env);
   tp.gates = reinterpret_cast<const tnrc::GateEntry*>(base + o_gates);
+  tp.merged = reinterpret_cast<const double2*>(base + o_merged);
   tp.mask = base + o_mask;
   tp.O = reinterpret_cast<double2*>(base + o_O);
   tp.gsp = nullptr;

@@ -41,23 +41,33 @@ struct GateEntry {    // one bond gate of one (sample, slice)
   double2 E[4];       // exp(-i tau lambda_j)
 };
 
+// One slot layout: byte layout, site offsets, capacities and the checkpoint
+// segmentation that fits the per-CTA work region in this layout.
+struct Lay {
+  SlotLayout L;
+  const int* site_off;         // [N] complex-element offsets of the sites in a slot
+  const int* dcap;             // [N+1] capacity of D[i]
+  int seg, nseg;               // checkpoint segment length and count, in truncated layers
+};
+
 struct TrajParams {
   int N, K, C, P, M, chi, T;
   double dt, eps;              // eps = max(cutoff, kZeroFloor)
-  int seg, nseg;               // checkpoint segment length (slices) and count
   int want_grad;
   int warps;                   // warps per CTA
   int slab_elems;              // complex elements of each warp's shared slab
-  const int* site_off;         // [N] complex-element offsets of the sites in a slot
-  SlotLayout L;
-  const unsigned char* in_slots;   // P canonical input slots
-  const unsigned char* tg_slots;   // P canonical target slots
-  unsigned char* work;             // per CTA: (2 + nseg + 3*seg) slots
+  Lay full;                    // capacities min(2^i, 2^(N-i), chi)
+  int packed_history;          // keep the forward history packed (no recomputation)
+  long long history_cap;       // upper bound on a CTA's packed-history bytes
+  const unsigned char* in_slots;   // P canonical input slots (full layout)
+  const unsigned char* tg_slots;   // P canonical target slots (full layout)
+  unsigned char* work;             // per CTA: 2 working slots, then packed history or checkpoints
   int64_t work_stride;             // bytes per CTA
   double2* warp_scratch;           // per warp: scratch_elems complex
   int64_t scratch_elems;
   double2* env_scratch;            // per CTA: 2*(N+1)*chi*chi complex
   const GateEntry* gates;          // [M][K][N-1]
+  const double2* merged;           // [M][K-1][N-1][16]: G[k+1] G[k] on even bonds
   const unsigned char* mask;       // [C][N]
   double2* O;                      // [T]
   double* gsp;                     // [T][K*C*N] or null

@@ -1,9 +1,12 @@
 // Persistent trajectory kernel: one CTA evaluates one trajectory (noise sample
 // s, input p) at a time and takes the next one from a device work counter.
 //
-//   forward  (Sec. II, Eq. circuit): K slices of layers A(dt/2) B(dt) A(dt/2);
-//            every two-site gate is followed by the truncated SVD; the warps of
-//            the CTA take the disjoint bonds of a layer in a fixed round-robin.
+//   forward  (Sec. II, Eq. circuit): K slices of A(dt/2) B(dt) A(dt/2), applied
+//            as the 2K+1 truncated layers A_0, B_0, A_0A_1, B_1, ..., B_{K-1},
+//            A_{K-1} (the two half layers at a slice boundary merged into one
+//            gate: the state is compressed once per time step); every
+//            two-site gate is followed by the truncated SVD; the warps of the
+//            CTA take the disjoint bonds of a layer in a fixed round-robin.
 //   overlap  (Sec. II state form): O = <t_p | a(T)> by a transfer-matrix sweep.
 //   gradient (App. A): the costate b_l = L_{l+1}^dag .. L_L^dag t is propagated
 //            backwards with the same truncated update; for every gate of layer
@@ -17,7 +20,8 @@
 namespace tnrc {
 
 // device counters: [0] updates [1] Jacobi sweeps [2] max bond [3] algorithmic
-// FP64 flops [4] reserved [5 + d] forward updates that left bond dimension d
+// FP64 flops [4] trajectories whose packed history did not fit and that were
+// redone with checkpoints [5 + d] forward updates that left bond dimension d
 constexpr int kCtrHist = 5;
 
 struct WarpCtx {
@@ -25,7 +29,7 @@ struct WarpCtx {
   double2* scratch;    // global, scratch_elems
   double* sig2;        // shared, kMaxDim
   int* perm;           // shared, kMaxDim
-  double2* small;      // shared, 48 complex (three 4x4 matrices)
+  double2* small;      // shared, 64 complex (four 4x4 matrices)
   int lane;
   long long sweeps;
   long long updates;
@@ -47,21 +51,45 @@ __device__ __forceinline__ const GateEntry& gate_at(const TrajParams& p, int s, 
   return p.gates[((size_t)s * p.K + k) * (p.N - 1) + b];
 }
 
+// Truncated layer l (0..2K): parity l&1; slices of its elementary gates k0 <= k1
+// (k0 == k1 unless the layer merges the half steps of slices k0 and k0+1).
+__device__ __forceinline__ void layer_slices(int l, int K, int& k0, int& k1) {
+  if (l & 1) {
+    k0 = k1 = (l - 1) >> 1;
+  } else if (l == 0) {
+    k0 = k1 = 0;
+  } else if (l == 2 * K) {
+    k0 = k1 = K - 1;
+  } else {
+    k0 = (l >> 1) - 1;
+    k1 = k0 + 1;
+  }
+}
+
+// The 4x4 gate of bond b in truncated layer l.
+__device__ __forceinline__ const double2* layer_gate(const TrajParams& p, int s, int l, int b) {
+  int k0, k1;
+  layer_slices(l, p.K, k0, k1);
+  if (k0 == k1) return gate_at(p, s, k0, b).G;
+  return p.merged + (((size_t)s * (p.K - 1) + k0) * (p.N - 1) + b) * 16;
+}
+
 // ---------------------------------------------------------------------------
 // Two-site update of bond b: theta = lam_{b-1} G (B_b B_{b+1}), truncated SVD,
 // B_{b+1} <- Y_k^dag, B_b <- Phi Y_k / |S_k|, lam_b <- S_k / |S_k|.
 // ---------------------------------------------------------------------------
-__device__ void two_site_update(const TrajParams& p, unsigned char* slot, int b, const GateEntry& ge,
+__device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char* slot, int b, const double2* G,
                                 bool adjoint, bool record, bool count, WarpCtx& w) {
   const int lane = w.lane;
   const int chi = p.chi;
+  const int lstride = Y.L.chi;
   int* D = slot_dims(slot);
   const int Dl = D[b], Dc = D[b + 1], Dr = D[b + 2];
   const int m = 2 * Dl, n = 2 * Dr;
-  double2* sites = slot_sites(slot, p.L);
-  double* lam = slot_lam(slot, p.L);
-  double2* A = sites + p.site_off[b];
-  double2* Bt = sites + p.site_off[b + 1];
+  double2* sites = slot_sites(slot, Y.L);
+  double* lam = slot_lam(slot, Y.L);
+  double2* A = sites + Y.site_off[b];
+  double2* Bt = sites + Y.site_off[b + 1];
   double2* T = (m * n <= p.slab_elems) ? w.slab : (w.scratch + (size_t)4 * chi * chi);
   double2* Phi = w.scratch;
 
@@ -69,7 +97,7 @@ __device__ void two_site_update(const TrajParams& p, unsigned char* slot, int b,
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) g[r * 4 + c] = adjoint ? cconj(ge.G[c * 4 + r]) : ge.G[r * 4 + c];
+    for (int c = 0; c < 4; ++c) g[r * 4 + c] = adjoint ? cconj(G[c * 4 + r]) : G[r * 4 + c];
 
   // Phase 1: Phi = G (B_b B_{b+1}) and theta^dagger (column (al s1), row (s2 ga)).
   double fro = 0.0;
@@ -88,7 +116,7 @@ __device__ void two_site_update(const TrajParams& p, unsigned char* slot, int b,
       cfma(acc[2], a1, b0);
       cfma(acc[3], a1, b1);
     }
-    const double ll = (b > 0) ? lam[(size_t)(b - 1) * chi + al] : 1.0;
+    const double ll = (b > 0) ? lam[(size_t)(b - 1) * lstride + al] : 1.0;
 #pragma unroll
     for (int s1 = 0; s1 < 2; ++s1)
 #pragma unroll
@@ -112,7 +140,11 @@ __device__ void two_site_update(const TrajParams& p, unsigned char* slot, int b,
 
   // Phase 3: rank, truncate.
   double kept2, tot2;
-  const int k = warp_rank_truncate(T, n, m, chi, p.eps, w.sig2, w.perm, lane, kept2, tot2);
+  int k = warp_rank_truncate(T, n, m, chi, p.eps, w.sig2, w.perm, lane, kept2, tot2);
+  if (k > Y.dcap[b + 1]) {  // cannot happen (k <= min(m, n, chi)); keeps memory in bounds regardless
+    k = Y.dcap[b + 1];
+    if (lane == 0) atomicOr(p.status, kStatusBadDims);
+  }
   if (lane == 0) {
     if (sw < 0) atomicOr(p.status, kStatusNoConverge);
     if (!(tot2 >= 0.0) || !(tot2 < 1e300) || !(kept2 > 0.0)) atomicOr(p.status, kStatusNaN);
@@ -128,7 +160,7 @@ __device__ void two_site_update(const TrajParams& p, unsigned char* slot, int b,
   const double inv_kn = rsqrt(kept2);
 
   // Phase 4: write lam_b, B_{b+1} = Y_k^dag, B_b = Phi Y_k / |S_k|.
-  double* lamw = lam + (size_t)b * chi;
+  double* lamw = lam + (size_t)b * lstride;
   for (int i = lane; i < k; i += 32) lamw[i] = sqrt(w.sig2[w.perm[i]]) * inv_kn;
   for (int it = lane; it < k * n; it += 32) {
     const int i = it / n, r = it - i * n;
@@ -147,6 +179,61 @@ __device__ void two_site_update(const TrajParams& p, unsigned char* slot, int b,
   __syncwarp();
   if (lane == 0) D[b + 1] = k;
   __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Read-only view of a stored state: a slot of a layout, or a packed record.
+// A packed record holds D[N+1], the site offsets off[N] (complex elements) and
+// the site tensors at their actual dimensions -- the layer history of the
+// costate sweep is kept in this form.
+// ---------------------------------------------------------------------------
+struct StateView {
+  const int* D;
+  const int* off;
+  const double2* sites;
+};
+
+__device__ __forceinline__ StateView slot_view(const unsigned char* slot, const Lay& Y) {
+  return StateView{slot_dims(slot), Y.site_off, slot_sites(slot, Y.L)};
+}
+
+__device__ __forceinline__ size_t packed_header(int N) { return ((size_t)(2 * N + 1) * 4 + 15) / 16 * 16; }
+
+__device__ __forceinline__ StateView packed_view(const unsigned char* rec, int N) {
+  const int* D = reinterpret_cast<const int*>(rec);
+  return StateView{D, D + N + 1, reinterpret_cast<const double2*>(rec + packed_header(N))};
+}
+
+// Bytes of the packed record of a slot (same value in every thread).
+__device__ __forceinline__ size_t packed_bytes(const int* D, int N) {
+  size_t e = 0;
+  for (int i = 0; i < N; ++i) e += (size_t)D[i] * 2 * D[i + 1];
+  return packed_header(N) + e * 16;
+}
+
+// CTA-wide: write the packed record of `slot` to `rec`.
+__device__ void pack_state(const TrajParams& p, const Lay& Y, const unsigned char* slot, unsigned char* rec) {
+  const int N = p.N;
+  const int* D = slot_dims(slot);
+  int* hd = reinterpret_cast<int*>(rec);
+  double2* out = reinterpret_cast<double2*>(rec + packed_header(N));
+  const double2* src = slot_sites(slot, Y.L);
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int i = 0; i <= N; ++i) hd[i] = D[i];
+    for (int i = 0; i < N; ++i) {
+      hd[N + 1 + i] = o;
+      o += D[i] * 2 * D[i + 1];
+    }
+  }
+  size_t o = 0;
+  for (int i = 0; i < N; ++i) {
+    const int cnt = D[i] * 2 * D[i + 1];
+    const double2* a = src + Y.site_off[i];
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) out[o + e] = a[e];
+    o += cnt;
+  }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -200,12 +287,12 @@ __device__ void env_right_step(const double2* Ein, int Dcr, int Dar, const doubl
 }
 
 // <t|a> by one warp.
-__device__ double2 warp_overlap(const TrajParams& p, const unsigned char* tslot, const unsigned char* aslot,
-                                WarpCtx& w) {
+__device__ double2 warp_overlap(const TrajParams& p, const Lay& Yt, const unsigned char* tslot, const Lay& Ya,
+                                const unsigned char* aslot, WarpCtx& w) {
   const int* Dt = slot_dims(tslot);
   const int* Da = slot_dims(aslot);
-  const double2* ts = slot_sites(tslot, p.L);
-  const double2* as = slot_sites(aslot, p.L);
+  const double2* ts = slot_sites(tslot, Yt.L);
+  const double2* as = slot_sites(aslot, Ya.L);
   const size_t cc = (size_t)p.chi * p.chi;
   double2* E0 = w.scratch;
   double2* E1 = w.scratch + cc;
@@ -213,7 +300,7 @@ __device__ double2 warp_overlap(const TrajParams& p, const unsigned char* tslot,
   if (w.lane == 0) E0[0] = make_double2(1.0, 0.0);
   __syncwarp();
   for (int i = 0; i < p.N; ++i) {
-    env_left_step(E0, Dt[i], Da[i], ts + p.site_off[i], Dt[i + 1], as + p.site_off[i], Da[i + 1], tmp, E1,
+    env_left_step(E0, Dt[i], Da[i], ts + Yt.site_off[i], Dt[i + 1], as + Ya.site_off[i], Da[i + 1], tmp, E1,
                   w.lane);
     double2* x = E0;
     E0 = E1;
@@ -222,18 +309,105 @@ __device__ double2 warp_overlap(const TrajParams& p, const unsigned char* tslot,
   return E0[0];
 }
 
+// dO/du for the parameters u of one elementary gate (slice k, bond b), given
+// the mixed two-site density rho it sees: tr(P_u Omega) with
+// Omega = V ((Gam^T) o (e^{i tau Lam} V^dag rho V)) V^dag (Daleckii-Krein),
+// accumulated as 2 Re(conj(O) dO) into the trajectory's gradient row.
+__device__ void gate_gradient(const TrajParams& p, const GateEntry& ge, const double2* rho, int k, int b, double2 wO,
+                              double* gsp_row, WarpCtx& w) {
+  const int lane = w.lane;
+  const int N = p.N;
+  double2* T1 = w.small + 16;
+  double2* T2 = w.small + 32;
+  double2* Om = w.small + 48;
+  const int ri = (lane & 15) >> 2, ci = lane & 3;
+  // T1 = V^dag rho
+  if (lane < 16) {
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) cfmac(acc, ge.V[l * 4 + ri], rho[l * 4 + ci]);
+    T1[lane] = acc;
+  }
+  __syncwarp();
+  // Omega' = Gam^T o (e^{i tau lam_i} (T1 V))  -> T2
+  if (lane < 16) {
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) cfma(acc, T1[ri * 4 + l], ge.V[l * 4 + ci]);
+    acc = cmulc(acc, ge.E[ri]);
+    T2[lane] = cmul(ge.Gam[ci * 4 + ri], acc);
+  }
+  __syncwarp();
+  // T1 = V Omega'
+  if (lane < 16) {
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) cfma(acc, ge.V[ri * 4 + l], T2[l * 4 + ci]);
+    T1[lane] = acc;
+  }
+  __syncwarp();
+  // Omega = T1 V^dag
+  if (lane < 16) {
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) cfmac(acc, ge.V[ci * 4 + l], T1[ri * 4 + l]);
+    Om[lane] = acc;
+  }
+  __syncwarp();
+  if (lane < 5) {
+    const double wl = (b == 0) ? 1.0 : 0.5;
+    const double wr = (b + 1 == N - 1) ? 1.0 : 0.5;
+    double2 v;
+    int c = -1, site = -1;
+    if (lane == 0) {  // X on the left site
+      v = make_double2(Om[8].x + Om[13].x + Om[2].x + Om[7].x, Om[8].y + Om[13].y + Om[2].y + Om[7].y);
+      v = cscale(v, wl);
+      c = 0;
+      site = b;
+    } else if (lane == 1) {  // Y on the left site: -i Om[2+s][s] + i Om[s][2+s]
+      const double2 d = make_double2(Om[2].x + Om[7].x - Om[8].x - Om[13].x, Om[2].y + Om[7].y - Om[8].y - Om[13].y);
+      v = cscale(make_double2(-d.y, d.x), wl);
+      c = 1;
+      site = b;
+    } else if (lane == 2) {  // X on the right site
+      v = make_double2(Om[4].x + Om[1].x + Om[14].x + Om[11].x, Om[4].y + Om[1].y + Om[14].y + Om[11].y);
+      v = cscale(v, wr);
+      c = 0;
+      site = b + 1;
+    } else if (lane == 3) {  // Y on the right site: -i Om[2s+1][2s] + i Om[2s][2s+1]
+      const double2 d = make_double2(Om[1].x + Om[11].x - Om[4].x - Om[14].x, Om[1].y + Om[11].y - Om[4].y - Om[14].y);
+      v = cscale(make_double2(-d.y, d.x), wr);
+      c = 1;
+      site = b + 1;
+    } else {  // ZZ
+      v = make_double2(Om[0].x - Om[5].x - Om[10].x + Om[15].x, Om[0].y - Om[5].y - Om[10].y + Om[15].y);
+      c = (p.C == 3) ? 2 : -1;
+      site = b;
+    }
+    if (c >= 0 && p.mask[c * N + site]) {
+      // dF contribution 2 Re(conj(O) dO)
+      const double contrib = 2.0 * (wO.x * v.x + wO.y * v.y);
+      gsp_row[((size_t)k * p.C + c) * N + site] += contrib;
+    }
+  }
+  __syncwarp();
+}
+
 // ---------------------------------------------------------------------------
 // Gradient of one layer: environments, mixed two-site densities, and
 // dO/du = tr(P_u Omega) with Omega = V ((Gam^T) o (e^{i tau Lam} V^dag rho V)) V^dag.
 // ---------------------------------------------------------------------------
-__device__ void layer_gradient(const TrajParams& p, const unsigned char* cslot, const unsigned char* aslot,
-                               int s, int k, int parity, double2 wO, double* gsp_row, WarpCtx& w, int warp) {
+__device__ void layer_gradient(const TrajParams& p, const Lay& Y, const unsigned char* cslot, const StateView av,
+                               int s, int l, double2 wO, double* gsp_row, WarpCtx& w, int warp) {
+  const int parity = l & 1;
   const int N = p.N, chi = p.chi;
   const size_t cc = (size_t)chi * chi;
   const int* Dc = slot_dims(cslot);
-  const int* Da = slot_dims(aslot);
-  const double2* cs = slot_sites(cslot, p.L);
-  const double2* as = slot_sites(aslot, p.L);
+  const int* Da = av.D;
+  const double2* cs = slot_sites(cslot, Y.L);
+  const double2* as = av.sites;
+  const int* so = Y.site_off;   // costate slot offsets
+  const int* ao = av.off;       // forward-state offsets
   double2* Lbuf = p.env_scratch + (size_t)blockIdx.x * 2 * (N + 1) * cc;
   double2* Rbuf = Lbuf + (size_t)(N + 1) * cc;
   const int lane = w.lane;
@@ -243,7 +417,7 @@ __device__ void layer_gradient(const TrajParams& p, const unsigned char* cslot, 
     if (lane == 0) Lbuf[0] = make_double2(1.0, 0.0);
     __syncwarp();
     for (int i = 0; i + 1 <= N - 2; ++i) {
-      env_left_step(Lbuf + i * cc, Dc[i], Da[i], cs + p.site_off[i], Dc[i + 1], as + p.site_off[i], Da[i + 1],
+      env_left_step(Lbuf + i * cc, Dc[i], Da[i], cs + so[i], Dc[i + 1], as + ao[i], Da[i + 1],
                     w.scratch, Lbuf + (i + 1) * cc, lane);
       w.alg += 16ull * Da[i + 1] * (unsigned long long)(Dc[i] * Da[i] + Dc[i + 1] * Dc[i]);
     }
@@ -251,8 +425,8 @@ __device__ void layer_gradient(const TrajParams& p, const unsigned char* cslot, 
     if (lane == 0) Rbuf[(size_t)N * cc] = make_double2(1.0, 0.0);
     __syncwarp();
     for (int i = N - 1; i >= 2; --i) {
-      env_right_step(Rbuf + (size_t)(i + 1) * cc, Dc[i + 1], Da[i + 1], cs + p.site_off[i], Dc[i],
-                     as + p.site_off[i], Da[i], w.scratch, Rbuf + (size_t)i * cc, lane);
+      env_right_step(Rbuf + (size_t)(i + 1) * cc, Dc[i + 1], Da[i + 1], cs + so[i], Dc[i],
+                     as + ao[i], Da[i], w.scratch, Rbuf + (size_t)i * cc, lane);
       w.alg += 16ull * Da[i] * (unsigned long long)(Dc[i + 1] * Da[i + 1] + Dc[i] * Dc[i + 1]);
     }
   }
@@ -265,10 +439,10 @@ __device__ void layer_gradient(const TrajParams& p, const unsigned char* cslot, 
     const int dal = Da[b], dam = Da[b + 1], dar = Da[b + 2];
     const double2* L = Lbuf + (size_t)b * cc;
     const double2* R = Rbuf + (size_t)(b + 2) * cc;
-    const double2* a0 = as + p.site_off[b];
-    const double2* a1 = as + p.site_off[b + 1];
-    const double2* c0 = cs + p.site_off[b];
-    const double2* c1 = cs + p.site_off[b + 1];
+    const double2* a0 = as + ao[b];
+    const double2* a1 = as + ao[b + 1];
+    const double2* c0 = cs + so[b];
+    const double2* c1 = cs + so[b + 1];
     w.alg += 8ull * dcl * (2ull * dam * dal + 4ull * dcr * dcm + 4ull * dar * dam + 4ull * dcr * dar + 16ull * dcr) +
              2048ull;
     double2* U1 = w.scratch;                        // [dcl][2][dam]
@@ -327,79 +501,29 @@ __device__ void layer_gradient(const TrajParams& p, const unsigned char* cslot, 
       if (lane < 16) rho[o] = acc;
     }
     __syncwarp();
-    const GateEntry& ge = gate_at(p, s, k, b);
-    double2* T1 = w.small + 16;
-    double2* T2 = w.small + 32;
-    const int ri = (lane & 15) >> 2, ci = lane & 3;
-    // T1 = V^dag rho
-    if (lane < 16) {
-      double2 acc = make_double2(0.0, 0.0);
+    int k0, k1;
+    layer_slices(l, p.K, k0, k1);
+    // the gate applied last in the layer sees rho; an earlier one sees G_last^dag rho G_last
+    gate_gradient(p, gate_at(p, s, k1, b), rho, k1, b, wO, gsp_row, w);
+    if (k0 != k1) {
+      const double2* G2 = gate_at(p, s, k1, b).G;
+      double2* T1 = w.small + 16;
+      const int ri = (lane & 15) >> 2, ci = lane & 3;
+      if (lane < 16) {  // T1 = rho G2
+        double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
-      for (int l = 0; l < 4; ++l) cfmac(acc, ge.V[l * 4 + ri], rho[l * 4 + ci]);
-      T1[lane] = acc;
-    }
-    __syncwarp();
-    // Omega' = Gam^T o (e^{i tau lam_i} (T1 V))  -> T2
-    if (lane < 16) {
-      double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int l = 0; l < 4; ++l) cfma(acc, T1[ri * 4 + l], ge.V[l * 4 + ci]);
-      acc = cmulc(acc, ge.E[ri]);
-      T2[lane] = cmul(ge.Gam[ci * 4 + ri], acc);
-    }
-    __syncwarp();
-    // T1 = V Omega'
-    if (lane < 16) {
-      double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int l = 0; l < 4; ++l) cfma(acc, ge.V[ri * 4 + l], T2[l * 4 + ci]);
-      T1[lane] = acc;
-    }
-    __syncwarp();
-    // Omega = T1 V^dag -> rho (reuse)
-    if (lane < 16) {
-      double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int l = 0; l < 4; ++l) cfmac(acc, ge.V[ci * 4 + l], T1[ri * 4 + l]);
-      rho[lane] = acc;
-    }
-    __syncwarp();
-    if (lane < 5) {
-      const double2* Om = rho;
-      const double wl = (b == 0) ? 1.0 : 0.5;
-      const double wr = (b + 1 == N - 1) ? 1.0 : 0.5;
-      double2 v;
-      int c = -1, site = -1;
-      if (lane == 0) {  // X on the left site
-        v = make_double2(Om[8].x + Om[13].x + Om[2].x + Om[7].x, Om[8].y + Om[13].y + Om[2].y + Om[7].y);
-        v = cscale(v, wl);
-        c = 0;
-        site = b;
-      } else if (lane == 1) {  // Y on the left site: -i Om[2+s][s] + i Om[s][2+s]
-        const double2 d = make_double2(Om[2].x + Om[7].x - Om[8].x - Om[13].x, Om[2].y + Om[7].y - Om[8].y - Om[13].y);
-        v = cscale(make_double2(-d.y, d.x), wl);
-        c = 1;
-        site = b;
-      } else if (lane == 2) {  // X on the right site
-        v = make_double2(Om[4].x + Om[1].x + Om[14].x + Om[11].x, Om[4].y + Om[1].y + Om[14].y + Om[11].y);
-        v = cscale(v, wr);
-        c = 0;
-        site = b + 1;
-      } else if (lane == 3) {  // Y on the right site: -i Om[2s+1][2s] + i Om[2s][2s+1]
-        const double2 d = make_double2(Om[1].x + Om[11].x - Om[4].x - Om[14].x, Om[1].y + Om[11].y - Om[4].y - Om[14].y);
-        v = cscale(make_double2(-d.y, d.x), wr);
-        c = 1;
-        site = b + 1;
-      } else {  // ZZ
-        v = make_double2(Om[0].x - Om[5].x - Om[10].x + Om[15].x, Om[0].y - Om[5].y - Om[10].y + Om[15].y);
-        c = (p.C == 3) ? 2 : -1;
-        site = b;
+        for (int q = 0; q < 4; ++q) cfma(acc, rho[ri * 4 + q], G2[q * 4 + ci]);
+        T1[lane] = acc;
       }
-      if (c >= 0 && p.mask[c * N + site]) {
-        // dF contribution 2 Re(conj(O) dO)
-        const double contrib = 2.0 * (wO.x * v.x + wO.y * v.y);
-        gsp_row[((size_t)k * p.C + c) * N + site] += contrib;
+      __syncwarp();
+      if (lane < 16) {  // rho <- G2^dag T1
+        double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cfmac(acc, G2[q * 4 + ri], T1[q * 4 + ci]);
+        rho[lane] = acc;
       }
+      __syncwarp();
+      gate_gradient(p, gate_at(p, s, k0, b), rho, k0, b, wO, gsp_row, w);
     }
     __syncwarp();
   }
@@ -407,37 +531,142 @@ __device__ void layer_gradient(const TrajParams& p, const unsigned char* cslot, 
 }
 
 // ---------------------------------------------------------------------------
-__device__ void copy_slot(const TrajParams& p, const unsigned char* src, unsigned char* dst) {
+// Copy the used part of a state slot; src and dst may use different layouts.
+// Returns 1 (and copies nothing) when a dimension exceeds dst's capacity.
+__device__ int copy_slot(const TrajParams& p, const Lay& Ys, const unsigned char* src, const Lay& Yd,
+                         unsigned char* dst) {
   __syncthreads();
   const int* Ds = slot_dims(src);
   int* Dd = slot_dims(dst);
   const int tid = threadIdx.x, nt = blockDim.x;
+  int bad = 0;
+  for (int i = tid; i <= p.N; i += nt) bad |= (Ds[i] > Yd.dcap[i]) ? 1 : 0;
+  if (__syncthreads_or(bad)) return 1;
   for (int i = tid; i <= p.N; i += nt) Dd[i] = Ds[i];
-  const double* ls = slot_lam(src, p.L);
-  double* ld = slot_lam(dst, p.L);
+  const double* ls = slot_lam(src, Ys.L);
+  double* ld = slot_lam(dst, Yd.L);
   for (int b = 0; b < p.N - 1; ++b) {
     const int d = Ds[b + 1];
-    for (int j = tid; j < d; j += nt) ld[(size_t)b * p.chi + j] = ls[(size_t)b * p.chi + j];
+    for (int j = tid; j < d; j += nt) ld[(size_t)b * Yd.L.chi + j] = ls[(size_t)b * Ys.L.chi + j];
   }
-  const double2* ss = slot_sites(src, p.L);
-  double2* sd = slot_sites(dst, p.L);
+  const double2* ss = slot_sites(src, Ys.L);
+  double2* sd = slot_sites(dst, Yd.L);
   for (int i = 0; i < p.N; ++i) {
     const int cnt = Ds[i] * 2 * Ds[i + 1];
-    const double2* a = ss + p.site_off[i];
-    double2* b = sd + p.site_off[i];
+    const double2* a = ss + Ys.site_off[i];
+    double2* b = sd + Yd.site_off[i];
     for (int e = tid; e < cnt; e += nt) b[e] = a[e];
+  }
+  __syncthreads();
+  return 0;
+}
+
+__device__ void apply_layer(const TrajParams& p, const Lay& Y, unsigned char* slot, int s, int l, bool adjoint,
+                           bool record, bool count, WarpCtx& w, int warp) {
+  const int parity = l & 1;
+  const int nb = (p.N - 1 - parity + 1) / 2;
+  for (int j = warp; j < nb; j += p.warps) {
+    const int b = parity + 2 * j;
+    two_site_update(p, Y, slot, b, layer_gate(p, s, l, b), adjoint, record, count, w);
   }
   __syncthreads();
 }
 
-__device__ void apply_layer(const TrajParams& p, unsigned char* slot, int s, int k, int parity, bool adjoint,
-                            bool record, bool count, WarpCtx& w, int warp) {
-  const int nb = (p.N - 1 - parity + 1) / 2;
-  for (int j = warp; j < nb; j += p.warps) {
-    const int b = parity + 2 * j;
-    two_site_update(p, slot, b, gate_at(p, s, k, b), adjoint, record, count, w);
+// One trajectory (sample s, input pi) with the CTA's work region `base`.
+//   packed = true : every layer state of the forward pass is kept as a packed
+//                   record in the region (no recomputation in the costate
+//                   sweep); returns 1 if the history outgrows the region.
+//   packed = false: checkpoints every Y.seg layers and recomputation of each
+//                   segment (fits by construction).
+__device__ int run_trajectory(const TrajParams& p, bool packed, unsigned char* base, int t, int s, int pi,
+                              WarpCtx& w, int warp, double* s_disc, int* s_maxk, double2* s_O) {
+  const Lay& Y = p.full;
+  const int lane = w.lane;
+  const size_t sb = (size_t)Y.L.bytes;
+  const int L = 2 * p.K + 1;  // truncated layers
+  unsigned char* a_slot = base;
+  unsigned char* c_slot = base + sb;
+  unsigned char* ckpt = base + 2 * sb;
+  unsigned char* segs = ckpt + (size_t)Y.nseg * sb;
+  long long* hpos = reinterpret_cast<long long*>(base + 2 * sb);  // packed mode: record offsets
+  unsigned char* harena = base + 2 * sb + (((size_t)L * 8 + 255) / 256) * 256;
+  const size_t hbytes = min((size_t)p.work_stride - (size_t)(harena - base), (size_t)p.history_cap);
+  const int KCN = p.K * p.C * p.N;
+  w.disc = 0.0;
+  w.maxk = 0;
+  copy_slot(p, Y, p.in_slots + (size_t)pi * sb, Y, a_slot);
+  // ---- forward ----
+  size_t pos = 0;
+  for (int l = 0; l < L; ++l) {
+    const int q = l / Y.seg;
+    if (p.want_grad && !packed && (l % Y.seg) == 0 && q < Y.nseg - 1) copy_slot(p, Y, a_slot, Y, ckpt + (size_t)q * sb);
+    apply_layer(p, Y, a_slot, s, l, false, true, true, w, warp);
+    if (p.want_grad) {
+      if (packed) {
+        const size_t need = packed_bytes(slot_dims(a_slot), p.N);
+        if (pos + need > hbytes) return 1;
+        pack_state(p, Y, a_slot, harena + pos);
+        if (threadIdx.x == 0) hpos[l] = (long long)pos;
+        pos += (need + 255) / 256 * 256;
+      } else if (q == Y.nseg - 1) {
+        copy_slot(p, Y, a_slot, Y, segs + (size_t)(l - q * Y.seg) * sb);
+      }
+    }
+  }
+  const unsigned char* tg = p.tg_slots + (size_t)pi * sb;
+  if (warp == 0) {
+    const double2 O = warp_overlap(p, Y, tg, Y, a_slot, w);
+    if (lane == 0) *s_O = O;
+    const int* Dt = slot_dims(tg);
+    const int* Da = slot_dims(a_slot);
+    for (int i = 0; i < p.N; ++i)
+      w.alg += 16ull * Da[i + 1] * (unsigned long long)(Dt[i] * Da[i] + Dt[i + 1] * Dt[i]);
+  }
+  if (lane == 0) {
+    s_disc[warp] = w.disc;
+    s_maxk[warp] = w.maxk;
   }
   __syncthreads();
+  const double2 O = *s_O;
+  if (threadIdx.x == 0) {
+    p.O[t] = O;
+    double d = 0.0;
+    int mk = 0;
+    for (int i = 0; i < p.warps; ++i) {
+      d += s_disc[i];
+      mk = max(mk, s_maxk[i]);
+    }
+    p.disc[t] = d;
+    atomicMax(&p.counters[2], (unsigned long long)mk);
+  }
+  if (!p.want_grad) return 0;
+  // ---- costate sweep ----
+  double* grow = p.gsp + (size_t)t * KCN;
+  for (int i = threadIdx.x; i < KCN; i += blockDim.x) grow[i] = 0.0;
+  copy_slot(p, Y, tg, Y, c_slot);
+  if (packed) {
+    for (int l = L - 1; l >= 0; --l) {
+      layer_gradient(p, Y, c_slot, packed_view(harena + hpos[l], p.N), s, l, O, grow, w, warp);
+      apply_layer(p, Y, c_slot, s, l, true, false, true, w, warp);
+    }
+    return 0;
+  }
+  for (int q = Y.nseg - 1; q >= 0; --q) {
+    const int l0 = q * Y.seg;
+    const int l1 = min(L, l0 + Y.seg);
+    if (q != Y.nseg - 1) {
+      unsigned char* ck = ckpt + (size_t)q * sb;
+      for (int l = l0; l < l1; ++l) {
+        apply_layer(p, Y, ck, s, l, false, false, false, w, warp);
+        copy_slot(p, Y, ck, Y, segs + (size_t)(l - l0) * sb);
+      }
+    }
+    for (int l = l1 - 1; l >= l0; --l) {
+      layer_gradient(p, Y, c_slot, slot_view(segs + (size_t)(l - l0) * sb, Y), s, l, O, grow, w, warp);
+      apply_layer(p, Y, c_slot, s, l, true, false, true, w, warp);
+    }
+  }
+  return 0;
 }
 
 __global__ void __launch_bounds__(kWarps * 32, 1) traj_kernel(TrajParams p) {
@@ -445,6 +674,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) traj_kernel(TrajParams p) {
   __shared__ int s_item;
   __shared__ double s_disc[kWarps];
   __shared__ int s_maxk[kWarps];
+  __shared__ double2 s_O;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   double2* slabs = reinterpret_cast<double2*>(smem_raw);
@@ -457,18 +687,12 @@ __global__ void __launch_bounds__(kWarps * 32, 1) traj_kernel(TrajParams p) {
   w.scratch = p.warp_scratch + ((size_t)blockIdx.x * p.warps + warp) * p.scratch_elems;
   w.sig2 = sig + (size_t)warp * kMaxDim;
   w.perm = perms + (size_t)warp * kMaxDim;
-  w.small = smalls + (size_t)warp * 48;
+  w.small = smalls + (size_t)warp * 64;
   w.lane = lane;
   w.sweeps = 0;
   w.updates = 0;
   w.alg = 0;
-
   unsigned char* base = p.work + (size_t)blockIdx.x * p.work_stride;
-  unsigned char* a_slot = base;
-  unsigned char* c_slot = base + p.L.bytes;
-  unsigned char* ckpt = base + 2 * p.L.bytes;
-  unsigned char* segs = ckpt + (size_t)p.nseg * p.L.bytes;
-  const int KCN = p.K * p.C * p.N;
 
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(p.work_counter, 1);
@@ -477,70 +701,19 @@ __global__ void __launch_bounds__(kWarps * 32, 1) traj_kernel(TrajParams p) {
     __syncthreads();
     if (t >= p.T) break;
     const int s = t / p.P, pi = t - s * p.P;
-    w.disc = 0.0;
-    w.maxk = 0;
-    copy_slot(p, p.in_slots + (size_t)pi * p.L.bytes, a_slot);
-    // ---- forward ----
-    for (int k = 0; k < p.K; ++k) {
-      const int q = k / p.seg;
-      if (p.want_grad && (k % p.seg) == 0 && q < p.nseg - 1) copy_slot(p, a_slot, ckpt + (size_t)q * p.L.bytes);
-      for (int li = 0; li < 3; ++li) {
-        apply_layer(p, a_slot, s, k, li == 1 ? 1 : 0, false, true, true, w, warp);
-        if (p.want_grad && q == p.nseg - 1)
-          copy_slot(p, a_slot, segs + (size_t)(3 * (k - q * p.seg) + li) * p.L.bytes);
+    bool redo = true;
+    if (p.want_grad && p.packed_history) {
+      const long long sw0 = w.sweeps, up0 = w.updates;
+      const unsigned long long al0 = w.alg;
+      redo = run_trajectory(p, true, base, t, s, pi, w, warp, s_disc, s_maxk, &s_O) != 0;
+      if (redo) {  // history outgrew the region: discard the attempt's counts, count the fallback
+        w.sweeps = sw0;
+        w.updates = up0;
+        w.alg = al0;
+        if (threadIdx.x == 0) atomicAdd(&p.counters[4], 1ull);
       }
     }
-    const unsigned char* tg = p.tg_slots + (size_t)pi * p.L.bytes;
-    __shared__ double2 s_O;
-    if (warp == 0) {
-      const double2 O = warp_overlap(p, tg, a_slot, w);
-      if (lane == 0) s_O = O;
-      for (int i = 0; i < p.N; ++i) {
-        const int* Dt = slot_dims(tg);
-        const int* Da = slot_dims(a_slot);
-        w.alg += 16ull * Da[i + 1] * (unsigned long long)(Dt[i] * Da[i] + Dt[i + 1] * Dt[i]);
-      }
-    }
-    if (lane == 0) {
-      s_disc[warp] = w.disc;
-      s_maxk[warp] = w.maxk;
-    }
-    __syncthreads();
-    const double2 O = s_O;
-    if (threadIdx.x == 0) {
-      p.O[t] = O;
-      double d = 0.0;
-      int mk = 0;
-      for (int i = 0; i < p.warps; ++i) {
-        d += s_disc[i];
-        mk = max(mk, s_maxk[i]);
-      }
-      p.disc[t] = d;
-      atomicMax(&p.counters[2], (unsigned long long)mk);
-    }
-    if (!p.want_grad) continue;
-    // ---- costate sweep ----
-    double* grow = p.gsp + (size_t)t * KCN;
-    for (int i = threadIdx.x; i < KCN; i += blockDim.x) grow[i] = 0.0;
-    copy_slot(p, tg, c_slot);
-    for (int q = p.nseg - 1; q >= 0; --q) {
-      const int k0 = q * p.seg;
-      const int k1 = min(p.K, k0 + p.seg);
-      if (q != p.nseg - 1) {
-        unsigned char* ck = ckpt + (size_t)q * p.L.bytes;
-        for (int k = k0; k < k1; ++k)
-          for (int li = 0; li < 3; ++li) {
-            apply_layer(p, ck, s, k, li == 1 ? 1 : 0, false, false, false, w, warp);
-            copy_slot(p, ck, segs + (size_t)(3 * (k - k0) + li) * p.L.bytes);
-          }
-      }
-      for (int l = 3 * (k1 - k0) - 1; l >= 0; --l) {
-        const int k = k0 + l / 3, li = l % 3;
-        const int parity = (li == 1) ? 1 : 0;
-        layer_gradient(p, c_slot, segs + (size_t)l * p.L.bytes, s, k, parity, O, grow, w, warp);
-        apply_layer(p, c_slot, s, k, parity, true, false, true, w, warp);
-      }
-    }
+    if (redo) run_trajectory(p, false, base, t, s, pi, w, warp, s_disc, s_maxk, &s_O);
   }
   if (lane == 0) {
     atomicAdd(&p.counters[0], (unsigned long long)w.updates);
@@ -565,5 +738,5 @@ extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, siz
 
 extern "C" size_t tnrc_traj_smem(int warps, int slab_elems) {
   return (size_t)warps * slab_elems * sizeof(double2) + (size_t)warps * tnrc::kMaxDim * (sizeof(double) + sizeof(int)) +
-         (size_t)warps * 48 * sizeof(double2);
+         (size_t)warps * 64 * sizeof(double2);
 }

@@ -1,0 +1,234 @@
+"""Serving loop for many concurrent robust-GRAPE optimisers on one GPU.
+
+Each request asks for F (and optionally dF/du) of one problem -- chain length,
+chi_max, slices, ensemble, inputs/targets -- at one control vector, with its
+own noise seed.  The server
+
+  * keeps one tnrc context per problem resident on the device (canonical
+    inputs/targets, gate tables, MPS and costate working slots) and reuses it
+    for every later request of that problem, as an optimiser's iterations do;
+  * admits a request when its context's device footprint fits the memory
+    budget next to the contexts already holding work (idle contexts are
+    destroyed first, least recently used, when memory is short);
+  * launches every admitted request at once on its context's own CUDA stream,
+    so requests that arrive while others run are admitted as slots and memory
+    free up and their kernels overlap on the device (continuous batching: the
+    block scheduler fills the SMs left free by one request's persistent CTAs
+    with the next request's);
+  * completes a request when its stream's event has fired, copying F and the
+    gradient back, and records arrival, start and finish times.
+
+Every evaluation is deterministic and independent of what else runs, so a
+request's result is the same alone and in any mix.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import threading
+import time
+from typing import Optional
+
+import numpy as np
+
+from .tnrc import Context, footprint
+
+
+@dataclasses.dataclass
+class Request:
+    """One evaluation.  ``key`` identifies the problem (requests with equal
+    keys share a resident context); inputs/targets are MPS objects (``pack()``)
+    or (bond_dims, data) pairs."""
+    key: str
+    N: int
+    K: int
+    dt: float
+    chi: int
+    M: int
+    C: int
+    inputs: list
+    targets: list
+    controls: np.ndarray
+    noise_seed: int
+    noise_dist: int
+    noise_scale: float
+    want_grad: bool = True
+    mask: Optional[np.ndarray] = None
+    cutoff: float = 1e-12
+    # filled by the server
+    arrival: float = 0.0
+    start: float = 0.0
+    finish: float = 0.0
+    F: Optional[float] = None
+    grad: Optional[np.ndarray] = None
+    error: Optional[str] = None
+
+    @property
+    def P(self):
+        return len(self.inputs)
+
+    @property
+    def latency(self):
+        return self.finish - self.arrival
+
+    def footprint(self):
+        return footprint(self.N, self.K, self.dt, self.chi, self.M, self.C, self.P, cutoff=self.cutoff,
+                         mask=self.mask)
+
+
+class _Slot:
+    """A resident context with its stream and device output buffers."""
+
+    def __init__(self, req: Request, device):
+        import torch
+        self.key = req.key
+        self.stream = torch.cuda.Stream(device=device)
+        self.ctx = Context(req.N, req.K, req.dt, req.chi, req.M, req.C, req.inputs, req.targets,
+                           cutoff=req.cutoff, mask=req.mask, stream=self.stream.cuda_stream)
+        self.bytes = req.footprint()
+        self.F = torch.zeros(1, dtype=torch.float64, device=device)
+        self.g = torch.zeros((req.K, req.C, req.N), dtype=torch.float64, device=device)
+        self.event = torch.cuda.Event()
+        self.busy: Optional[Request] = None
+        self.last_used = 0.0
+
+    def launch(self, req: Request):
+        import torch
+        with torch.cuda.stream(self.stream):
+            self.ctx.set_controls(req.controls)
+            self.ctx.sample_noise(req.noise_seed, req.noise_dist, req.noise_scale)
+            self.ctx.evaluate_dev(self.F.data_ptr(), self.g.data_ptr() if req.want_grad else 0)
+            self.event.record(self.stream)
+        self.busy = req
+
+    def collect(self):
+        req = self.busy
+        self.ctx.sync()
+        req.F = float(self.F.item())
+        req.grad = self.g.cpu().numpy().copy() if req.want_grad else None
+        self.busy = None
+        return req
+
+    def close(self):
+        self.ctx.close()
+
+
+class Server:
+    """Continuous-batching server on one device.
+
+    mem_budget: device bytes the resident contexts may hold (default: 60% of
+    the free memory at start); max_inflight: requests on the device at once."""
+
+    def __init__(self, mem_budget: Optional[int] = None, max_inflight: int = 8, device: int = 0):
+        import torch
+        self.device = torch.device("cuda", device)
+        if mem_budget is None:
+            free, _ = torch.cuda.mem_get_info(self.device)
+            mem_budget = int(0.6 * free)
+        self.mem_budget = mem_budget
+        self.max_inflight = max_inflight
+        self.pending = collections.deque()
+        self.slots: list = []
+        self.done: list = []
+        self.lock = threading.Lock()
+        self.cv = threading.Condition(self.lock)
+        self.stop = False
+        self.admitted = 0
+        self.peak_inflight = 0
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
+
+    # ---- client side ----
+    def submit(self, req: Request) -> Request:
+        req.arrival = time.perf_counter()
+        with self.cv:
+            self.pending.append(req)
+            self.cv.notify()
+        return req
+
+    def drain(self, timeout: float = 3600.0):
+        """Wait until every submitted request has finished."""
+        t0 = time.perf_counter()
+        with self.cv:
+            while self.pending or any(s.busy for s in self.slots):
+                if time.perf_counter() - t0 > timeout:
+                    raise TimeoutError("requests still pending")
+                self.cv.wait(0.01)
+
+    def close(self):
+        with self.cv:
+            self.stop = True
+            self.cv.notify()
+        self.thread.join()
+        for s in self.slots:
+            s.close()
+        self.slots = []
+
+    # ---- server side ----
+    def _held(self):
+        return sum(s.bytes for s in self.slots)
+
+    def _admit(self, req: Request) -> bool:
+        idle = [s for s in self.slots if s.busy is None and s.key == req.key]
+        if idle:
+            slot = idle[0]
+        else:
+            need = req.footprint()
+            if need > self.mem_budget:
+                req.error = "request footprint %d B exceeds the server budget %d B" % (need, self.mem_budget)
+                req.finish = time.perf_counter()
+                self.done.append(req)
+                return True
+            # evict idle contexts of other problems, least recently used first
+            while self._held() + need > self.mem_budget:
+                idle_any = sorted((s for s in self.slots if s.busy is None), key=lambda s: s.last_used)
+                if not idle_any:
+                    return False
+                victim = idle_any[0]
+                victim.close()
+                self.slots.remove(victim)
+            import torch
+            with torch.cuda.device(self.device):
+                slot = _Slot(req, self.device)
+            self.slots.append(slot)
+        req.start = time.perf_counter()
+        slot.launch(req)
+        self.admitted += 1
+        return True
+
+    def _loop(self):
+        import torch
+        torch.cuda.set_device(self.device)
+        while True:
+            with self.cv:
+                if self.stop:
+                    return
+                # complete finished requests
+                for s in self.slots:
+                    if s.busy is not None and s.event.query():
+                        req = s.collect()
+                        req.finish = time.perf_counter()
+                        s.last_used = req.finish
+                        self.done.append(req)
+                # admit in arrival order while slots and memory allow
+                inflight = sum(1 for s in self.slots if s.busy is not None)
+                while self.pending and inflight < self.max_inflight:
+                    if not self._admit(self.pending[0]):
+                        break
+                    self.pending.popleft()
+                    inflight = sum(1 for s in self.slots if s.busy is not None)
+                self.peak_inflight = max(self.peak_inflight, inflight)
+                self.cv.notify_all()
+                if not self.pending and inflight == 0:
+                    self.cv.wait(0.01)
+            time.sleep(0.0002)
+
+
+def latency_stats(reqs):
+    """p50 / p99 latency (s) and throughput (requests/s) of finished requests."""
+    lat = np.array([r.latency for r in reqs if r.error is None])
+    if len(lat) == 0:
+        return {"n": 0}
+    span = max(r.finish for r in reqs) - min(r.arrival for r in reqs)
+    return {"n": int(len(lat)), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "throughput_rps": len(lat) / span if span > 0 else None}

@@ -35,7 +35,8 @@ class Problem(ctypes.Structure):
                 ("dt", ctypes.c_double), ("chi_max", ctypes.c_int32), ("sv_cutoff", ctypes.c_double),
                 ("n_samples", ctypes.c_int32), ("n_controls", ctypes.c_int32), ("n_inputs", ctypes.c_int32),
                 ("control_mask", ctypes.POINTER(ctypes.c_uint8)), ("g_fixed", ctypes.POINTER(ctypes.c_double)),
-                ("checkpoint_every", ctypes.c_int32)]
+                ("checkpoint_every", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32)]
 
 
 class MPSDesc(ctypes.Structure):
@@ -47,7 +48,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("updates", ctypes.c_int64), ("jacobi_sweeps", ctypes.c_int64), ("max_bond", ctypes.c_int32),
                 ("hist_len", ctypes.c_int32), ("bond_hist", ctypes.c_int64 * 65),
                 ("discarded_weight", ctypes.c_double), ("last_ms", ctypes.c_double),
-                ("alg_flops", ctypes.c_double), ("traj_ms", ctypes.c_double), ("traj_launches", ctypes.c_int64)]
+                ("alg_flops", ctypes.c_double), ("traj_ms", ctypes.c_double), ("traj_launches", ctypes.c_int64),
+                ("restarts", ctypes.c_int64)]
 
 
 _LIB = None
@@ -118,7 +120,8 @@ def _pack(state):
     return dims, data
 
 
-def make_problem(N, K, dt, chi, M, C, P, cutoff=1e-12, mask=None, g_fixed=None, checkpoint_every=0):
+def make_problem(N, K, dt, chi, M, C, P, cutoff=1e-12, mask=None, g_fixed=None, checkpoint_every=0, warps=0,
+                 ctas_per_sm=0):
     """A ``Problem`` plus the arrays it points to (keep both alive)."""
     keep = []
     pb = Problem()
@@ -134,6 +137,8 @@ def make_problem(N, K, dt, chi, M, C, P, cutoff=1e-12, mask=None, g_fixed=None, 
         keep.append(g)
         pb.g_fixed = _dp(g)
     pb.checkpoint_every = checkpoint_every
+    pb.warps_per_cta = warps
+    pb.ctas_per_sm = ctas_per_sm
     return pb, keep
 
 
@@ -175,13 +180,14 @@ class Context:
 
     def __init__(self, N: int, K: int, dt: float, chi: int, M: int, C: int, inputs: Sequence, targets: Sequence,
                  cutoff: float = 1e-12, mask=None, g_fixed=None, checkpoint_every: int = 0,
-                 stream: Optional[int] = None):
+                 stream: Optional[int] = None, warps: int = 0, ctas_per_sm: int = 0):
         L = lib()
         self.N, self.K, self.C, self.M, self.P = N, K, C, M, len(inputs)
         self.stream = int(stream or 0)
         if len(targets) != self.P:
             raise ValueError("inputs and targets differ in length")
-        pb, keep = make_problem(N, K, dt, chi, M, C, self.P, cutoff, mask, g_fixed, checkpoint_every)
+        pb, keep = make_problem(N, K, dt, chi, M, C, self.P, cutoff, mask, g_fixed, checkpoint_every, warps,
+                                ctas_per_sm)
         packs = [_pack(s) for s in list(inputs) + list(targets)]
         descs = (MPSDesc * len(packs))()
         for d, (dims, data) in zip(descs, packs):
@@ -265,4 +271,4 @@ class Context:
         return {"updates": s.updates, "jacobi_sweeps": s.jacobi_sweeps, "max_bond": s.max_bond,
                 "bond_hist": [int(s.bond_hist[i]) for i in range(s.hist_len)],
                 "discarded_weight": s.discarded_weight, "last_ms": s.last_ms, "alg_flops": s.alg_flops,
-                "traj_ms": s.traj_ms, "traj_launches": s.traj_launches}
+                "traj_ms": s.traj_ms, "traj_launches": s.traj_launches, "restarts": s.restarts}

@@ -158,11 +158,14 @@ def test_mps_state_matches_dense_vector_elementwise():
     pb = mkpb(N, K, dt, 3, 8, u, synth.control_mask(3, N, "all"), rng.normal(0, 0.1, N - 1), ins, ins)
     B, lam = mps.canonicalize(pb.inputs[0], pb.chi, pb.eps)
     a = dense.mps_vector(pb.inputs[0])
-    for (k, par, tau) in robust.layers(K, dt):
+    for (par, group) in robust.merged_layers(K, dt):
         for b in range(par, N - 1, 2):
-            G, _, _ = robust.bond_gate(pb, 0, k, b, tau)
-            mps.two_site_update(B, lam, b, G, pb.chi, pb.eps)
-            a = dense.apply_two_site(a, G, b, N)
+            Mg = np.eye(4, dtype=complex)
+            for (k, tau) in group:
+                G, _, _ = robust.bond_gate(pb, 0, k, b, tau)
+                Mg = G @ Mg
+                a = dense.apply_two_site(a, G, b, N)
+            mps.two_site_update(B, lam, b, Mg, pb.chi, pb.eps)
     v = mps.to_dense(B)
     assert np.max(np.abs(v - a)) < 1e-12
     # Schmidt values of every bond = singular values of the dense reshape
@@ -258,6 +261,17 @@ def test_bond_hamiltonians_sum_to_system_hamiltonian():
 
 
 # ----------------------------------------------------------------- invariants
+def test_merged_schedule_is_the_elementary_sequence():
+    K, dt = 4, 0.1
+    flat = [(k, par, tau) for (par, grp) in robust.merged_layers(K, dt) for (k, tau) in grp
+            for _ in [0]]
+    # the merged layers list the elementary layers in the same time order
+    elem = robust.layers(K, dt)
+    assert [(k, tau) for (k, _, tau) in flat] == [(k, tau) for (k, _, tau) in elem]
+    assert [p for (p, _) in robust.merged_layers(K, dt)] == [0] + [1, 0] * K
+    assert len(robust.merged_layers(K, dt)) == 2 * K + 1
+
+
 def test_costate_overlap_is_constant_over_layers():
     N, K, dt = 6, 4, 0.2
     rng = np.random.default_rng(91)
@@ -265,14 +279,16 @@ def test_costate_overlap_is_constant_over_layers():
     ins = rand_products(N, 1, 92)
     tgs = rand_products(N, 1, 93)
     pb = mkpb(N, K, dt, 3, 8, u, synth.control_mask(3, N, "all"), rng.normal(0, .1, N - 1), ins, tgs)
-    sched = robust.layers(K, dt)
+    sched = robust.merged_layers(K, dt)
     B, lam = mps.canonicalize(pb.inputs[0], 8, 1e-12)
     states = [[x.copy() for x in B]]
     gl = []
-    for (k, par, tau) in sched:
+    for (par, group) in sched:
         gg = {}
         for b in range(par, N - 1, 2):
-            G, _, _ = robust.bond_gate(pb, 0, k, b, tau)
+            G = np.eye(4, dtype=complex)
+            for (k, tau) in group:
+                G = robust.bond_gate(pb, 0, k, b, tau)[0] @ G
             gg[b] = G
             mps.two_site_update(B, lam, b, G, 8, 1e-12)
         gl.append(gg)

@@ -89,10 +89,17 @@ def test_hard_truncation_chi_4():
     assert grad_close(g, go)
 
 
-def test_checkpoint_segments_do_not_change_results():
+def test_checkpoint_segments_do_not_change_results(monkeypatch):
+    """Checkpoint/recompute segmentations (history cap 0 forces that path) and
+    the packed history give bitwise the same result."""
     w = synth.WORKLOADS["x8"].replace(K=7, M=2, P=2)
     u, mask, J, ins, tgs = case(w)
     res = []
+    ctx = gpu_context(w, ins, tgs, mask)
+    ctx.set_controls(u)
+    ctx.set_noise(J)
+    res.append(ctx.fidelity_grad())
+    monkeypatch.setenv("TNRC_HISTORY_CAP", "0")
     for ce in (1, 3, 7, 0):
         ctx = gpu_context(w, ins, tgs, mask, checkpoint_every=ce)
         ctx.set_controls(u)
@@ -171,3 +178,25 @@ def test_full_size_sampled_trajectories(name):
     Fo, go, _ = robust.ensemble(oracle_problem(w1, u, mask, J, ins, tgs))
     assert abs(F - Fo) <= TOL_F
     assert grad_close(g, go)
+
+
+def test_packed_history_and_checkpoint_fallback_agree(monkeypatch):
+    """The costate sweep reads the forward history packed (no recomputation)
+    when it fits the CTA's region; a history cap of 0 forces every trajectory
+    onto the checkpoint/recompute path.  Results must be identical."""
+    w = synth.WORKLOADS["ghz30"].replace(N=12, K=5, chi=32, M=2, P=1, u_sigma=1.5, dt=0.25)
+    u, mask, J, ins, tgs = case(w)
+    out = {}
+    for cap in ("none", "0"):
+        if cap == "none":
+            monkeypatch.delenv("TNRC_HISTORY_CAP", raising=False)
+        else:
+            monkeypatch.setenv("TNRC_HISTORY_CAP", cap)
+        ctx = gpu_context(w, ins, tgs, mask)
+        ctx.set_controls(u)
+        ctx.set_noise(J)
+        out[cap] = ctx.fidelity_grad()
+        st = ctx.stats()
+        assert st["restarts"] == (w.M * w.P if cap == "0" else 0)
+    assert out["0"][0] == out["none"][0]
+    assert np.array_equal(out["0"][1], out["none"][1])
