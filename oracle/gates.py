@@ -1,12 +1,14 @@
 """Two-site gates of the second-order TEBD slice (Sec. II, Eq. circuit, with
-the Hamiltonian of Eq. sysH and ZZ-only crosstalk).
+the Hamiltonian of Eq. sysH and the crosstalk of Eq. Hp).
 
 Bond b couples sites b and b+1.  Its Hamiltonian in the basis
 |s_b s_{b+1}> (index 2 s_b + s_{b+1}) is
 
-  h_b = c_b Z(x)Z + wL (x_b X + y_b Y)(x)I + wR I(x)(x_{b+1} X + y_{b+1} Y)
+  h_b = c_b Z(x)Z + J^x_b X(x)X + J^y_b Y(x)Y
+        + wL (x_b X + y_b Y)(x)I + wR I(x)(x_{b+1} X + y_{b+1} Y)
 
-with c_b = g_b + J_b (tunable plus parasitic ZZ) and single-site weights
+with c_b = g_b + J^z_b (tunable plus parasitic ZZ; J^x = J^y = 0 for pure ZZ
+crosstalk, all three for the Heisenberg-type crosstalk of Eq. Hp) and weights
 wL = 1 if b is the first bond else 1/2, wR = 1 if b is the last bond else 1/2,
 so that summing h_b over all bonds gives H of Eq. sysH.  The gate is the exact
 4x4 exponential G = exp(-i tau h_b) through the Hermitian eigendecomposition
@@ -26,11 +28,11 @@ def bond_weights(N: int, b: int):
     return wl, wr
 
 
-def bond_hamiltonian(N, b, xl, yl, xr, yr, c):
-    """h_b for left-site drives (xl, yl), right-site drives (xr, yr) and ZZ
-    coefficient c."""
+def bond_hamiltonian(N, b, xl, yl, xr, yr, c, jx=0.0, jy=0.0):
+    """h_b for left-site drives (xl, yl), right-site drives (xr, yr), ZZ
+    coefficient c and the XX, YY crosstalk strengths jx, jy (Eq. Hp)."""
     wl, wr = bond_weights(N, b)
-    return (c * np.kron(Z, Z)
+    return (c * np.kron(Z, Z) + jx * np.kron(X, X) + jy * np.kron(Y, Y)
             + wl * np.kron(xl * X + yl * Y, I2)
             + wr * np.kron(I2, xr * X + yr * Y))
 

@@ -76,19 +76,23 @@ def merged_layers(K, dt):
 
 
 def bond_params(pb: Problem, s, k, b):
-    """(xl, yl, xr, yr, c) of bond b in slice k for noise sample s; a masked
-    control slot does not enter the Hamiltonian."""
+    """(xl, yl, xr, yr, c, jx, jy) of bond b in slice k for noise sample s; a
+    masked control slot does not enter the Hamiltonian.  J[M][N-1] is ZZ
+    crosstalk; J[M][N-1][3] = (J^x, J^y, J^z) the Heisenberg type (Eq. Hp)."""
     u, m = pb.u, pb.mask
     xl = u[k, 0, b] * m[0, b]
     yl = u[k, 1, b] * m[1, b]
     xr = u[k, 0, b + 1] * m[0, b + 1]
     yr = u[k, 1, b + 1] * m[1, b + 1]
-    c = pb.J[s, b]
+    if pb.J.ndim == 3:
+        jx, jy, c = pb.J[s, b]
+    else:
+        jx, jy, c = 0.0, 0.0, pb.J[s, b]
     if pb.C == 3:
         c += u[k, 2, b] * m[2, b]
     if pb.g_fixed is not None:
         c += pb.g_fixed[k, b]
-    return xl, yl, xr, yr, c
+    return xl, yl, xr, yr, c, jx, jy
 
 
 def param_slots(pb: Problem, k, b):

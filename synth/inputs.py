@@ -262,6 +262,7 @@ class Workload:
     g_bonds: str = "none"
     sv_cutoff: float = 1e-12
     u_sigma: float = 0.5
+    crosstalk: int = 1       # 1: ZZ (J^z); 3: J^x XX + J^y YY + J^z ZZ (Eq. Hp)
 
     @property
     def trajectories(self) -> int:

@@ -258,6 +258,68 @@ def test_bond_hamiltonians_sum_to_system_hamiltonian():
     ref = sum(x[i] * op(PX, i) + y[i] * op(PY, i) for i in range(N))
     ref = ref + sum(c[b] * op(PZ, b) @ op(PZ, b + 1) for b in range(N - 1))
     assert np.max(np.abs(H - ref)) < 1e-13
+    # Heisenberg-type crosstalk terms (Eq. Hp)
+    jx, jy = rng.normal(size=N - 1), rng.normal(size=N - 1)
+    H2 = np.zeros((2 ** N, 2 ** N), dtype=complex)
+    for b in range(N - 1):
+        h = gates.bond_hamiltonian(N, b, x[b], y[b], x[b + 1], y[b + 1], c[b], jx[b], jy[b])
+        H2 += np.kron(np.kron(np.eye(2 ** b), h), np.eye(2 ** (N - b - 2)))
+    ref2 = ref + sum(jx[b] * op(PX, b) @ op(PX, b + 1) + jy[b] * op(PY, b) @ op(PY, b + 1) for b in range(N - 1))
+    assert np.max(np.abs(H2 - ref2)) < 1e-13
+
+
+def test_heisenberg_crosstalk_two_site_closed_form():
+    """u = 0, one bond: (J^x XX + J^y YY) couples |01> and |10> with strength
+    J^x + J^y, J^z ZZ is a phase on that subspace, so <01|U(T)|01> has modulus
+    |cos(T (J^x + J^y))|."""
+    N, K, dt = 2, 7, 0.13
+    jx, jy, jz = 0.31, -0.12, 0.27
+    one = synth.MPS([np.array([1.0, 0.0]).reshape(1, 2, 1), np.array([0.0, 1.0]).reshape(1, 2, 1)])
+    pb = mkpb(N, K, dt, 2, 2, np.zeros((K, 2, N)), synth.control_mask(2, N), np.array([[[jx, jy, jz]]]),
+              [one], [one])
+    F, _, _ = robust.ensemble(pb, want_grad=False)
+    assert abs(F - np.cos(K * dt * (jx + jy)) ** 2) < 1e-13
+
+
+def test_isotropic_xy_crosstalk_keeps_the_polarised_state():
+    """With J^x = J^y on every bond and no drive, |0...0> is an eigenstate of
+    every bond gate, so F = 1 for input = target = |0...0>."""
+    N, K, dt = 7, 5, 0.2
+    rng = np.random.default_rng(123)
+    jxy = rng.uniform(-0.3, 0.3, size=N - 1)
+    J = np.stack([jxy, jxy, rng.uniform(-0.3, 0.3, size=N - 1)], axis=1)[None]
+    z = synth.zero_state(N)
+    pb = mkpb(N, K, dt, 3, 8, np.zeros((K, 3, N)), synth.control_mask(3, N, "all"), J, [z], [z])
+    F, g, _ = robust.ensemble(pb)
+    assert abs(F - 1.0) < 1e-13
+    assert np.max(np.abs(g)) < 1e-12
+
+
+def test_heisenberg_crosstalk_mps_equals_dense_and_fd():
+    N, K, dt = 6, 4, 0.15
+    rng = np.random.default_rng(131)
+    u = rng.normal(0, 0.7, size=(K, 3, N))
+    mask = synth.control_mask(3, N, "all")
+    J = noise.sample_J(5, 2, N, 0, 0.2, terms=3)
+    ins = rand_products(N, 2, 132)
+    tgs = rand_products(N, 2, 133)
+    pb = mkpb(N, K, dt, 3, 8, u, mask, J, ins, tgs)
+    for s in range(2):
+        o1, d1 = robust.trajectory(pb, s, 1)
+        o2, d2 = dense.trajectory(pb, s, 1)
+        assert abs(o1 - o2) < 1e-12 and np.max(np.abs(d1 - d2)) < 1e-12
+    F, g, _ = robust.ensemble(pb)
+    h = 1e-6
+    for _ in range(8):
+        idx = tuple(int(rng.integers(0, n)) for n in u.shape)
+        if not mask[idx[1], idx[2]]:
+            continue
+        up, um = u.copy(), u.copy()
+        up[idx] += h
+        um[idx] -= h
+        Fp, _, _ = robust.ensemble(mkpb(N, K, dt, 3, 8, up, mask, J, ins, tgs), want_grad=False)
+        Fm, _, _ = robust.ensemble(mkpb(N, K, dt, 3, 8, um, mask, J, ins, tgs), want_grad=False)
+        assert abs((Fp - Fm) / (2 * h) - g[idx]) < 1e-6 * max(1e-3, np.max(np.abs(g)))
 
 
 # ----------------------------------------------------------------- invariants
@@ -360,6 +422,13 @@ def test_splitmix64_published_vectors():
             continue
         seed, i, out = (int(x) for x in line.split())
         assert noise.splitmix64(seed, i) == out
+
+
+def test_three_term_noise_uses_consecutive_counters():
+    J3 = noise.sample_J(8, 4, 6, 0, 0.1, terms=3)
+    flat = noise.sample_J(8, 4 * 3, 6, 0, 0.1)          # same stream, one term per "bond"
+    assert J3.shape == (4, 5, 3)
+    assert np.array_equal(J3.reshape(-1), flat.reshape(-1)[: 4 * 5 * 3])
 
 
 def test_noise_distributions():
