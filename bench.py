@@ -185,8 +185,10 @@ def gpu_arm(args, w):
     ins, tgs = w.states()
     mask = w.mask()
     u = w.controls()
+    from paper_2603_03639_gb300 import autotune
+    tuned = autotune.lookup(w.N, w.K, w.chi, w.M, w.P, w.C, grad=True)
     ctx = Context(w.N, w.K, w.dt, w.chi, w.M, w.C, ins, tgs, cutoff=w.sv_cutoff, mask=mask,
-                  stream=stream.cuda_stream)
+                  stream=stream.cuda_stream, warps=tuned[0], ctas_per_sm=tuned[1])
     u_dev = torch.tensor(u, dtype=torch.float64, device=dev)
     F_dev = torch.zeros(1, dtype=torch.float64, device=dev)
     g_dev = torch.zeros(u.shape, dtype=torch.float64, device=dev)
@@ -266,6 +268,11 @@ def gpu_arm(args, w):
     KCN = w.K * w.C * w.N
 
     peak = fp64_peak_tflops()
+    from paper_2603_03639_gb300.tnrc import measure_fp64_peak
+    probe = torch.empty(4 * 256 * torch.cuda.get_device_properties(dev).multi_processor_count,
+                        dtype=torch.float64, device=dev)
+    torch.cuda.synchronize(dev)
+    measured_peak = measure_fp64_peak(probe.data_ptr(), probe.numel() * 8) / 1e3
     achieved = (alg / launches) / (traj_ms / launches / 1000.0) / 1e12 if launches else None
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traj_kernel_traffic.json")
@@ -284,10 +291,15 @@ def gpu_arm(args, w):
                        l2="flushed between timed steps (512 MB write, outside the per-step events)"),
         "e2e": {"value": world * w.slice_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": KCN * 8,
                 "d2h_bytes_per_step": 8 + KCN * 8},
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": 6 * args.steps,
+        "launch_shape": {"warps_per_cta": tuned[0] or "default", "ctas_per_sm": tuned[1] or 1,
+                         "source": "autotune cache" if tuned[0] else "default"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "kernel": "tnrc::traj_kernel", "peak_source": "derived FP64 FMA peak: 2 DFMA/clk/SM x 152 SMs x 2070 MHz"},
+                     "kernel": "tnrc::traj_kernel",
+                     "peak_source": "derived FP64 FMA peak: 2 DFMA/clk/SM x 152 SMs x 2070 MHz",
+                     "measured_fp64_fma_peak": measured_peak,
+                     "frac_of_measured": (achieved / measured_peak) if achieved and measured_peak else None},
         "clocks": clk.summary(),
         "workload_stats": {"alg_flops_per_step": alg / args.steps, "traj_kernel_ms_per_step": traj_ms / args.steps,
                            "max_bond": maxb, "bond_hist": hist.tolist(), "discarded_weight": disc / args.steps,
@@ -311,8 +323,10 @@ def serving_problems(seed=41):
     """Eight resident problems ("optimisers") drawn like the mixed serving
     workload -- N in {8, 20, 30, 50}, chi in {16, 32, 64}, K, M log-uniform --
     scaled (K in [20, 50], M in [4, 32]) so that a rate sweep ends in minutes.
-    N=8: parallel X (P=4); N=20: Heisenberg ground state from |0..0>; N=30: GHZ;
-    N=50: parallel X or CNOT by the problem's parity."""
+    N=8: parallel X (P=4); N=20: Heisenberg ground state from |0..0> with chi 16
+    (the paper truncates that target at D = 20; at chi 64 its costate grows to
+    64-wide bonds and one request takes minutes); N=30: GHZ; N=50: parallel X
+    or CNOT by the problem's parity."""
     rng = np.random.default_rng(seed)
     probs = []
     heis = {}
@@ -324,7 +338,7 @@ def serving_problems(seed=41):
         if N == 8:
             w = synth.WORKLOADS["x8"].replace(chi=min(chi, 16), K=K, M=M)
         elif N == 20:
-            w = synth.Workload("heis20", N=20, chi=chi, K=K, dt=0.05, C=3, M=M, P=1, noise_dist=0,
+            w = synth.Workload("heis20", N=20, chi=16, K=K, dt=0.05, C=3, M=M, P=1, noise_dist=0,
                                noise_scale=0.05, seed_u=100 + j, seed_J=200 + j, seed_in=300 + j,
                                target="heisenberg", g_bonds="all")
         elif N == 30:
@@ -382,7 +396,9 @@ def serving_arm(args):
     rows = []
     for rate in rates:
         served, rs = serving_run(probs, rate, args.requests, 8, 1000 + int(rate * 10))
+        print("served at %g req/s: %s" % (rate, served), file=sys.stderr, flush=True)
         plain, rp = serving_run(probs, rate, args.requests, 1, 1000 + int(rate * 10))
+        print("plain at %g req/s: %s" % (rate, plain), file=sys.stderr, flush=True)
         same = all(a.F == b.F and (a.grad is None or np.array_equal(a.grad, b.grad)) for a, b in zip(rs, rp))
         rows.append({"offered_rps": rate, "served": served, "plain": plain, "results_identical": same})
     line = {"metric": "served p50/p99 latency and throughput vs plain sequential GPU calls",
@@ -401,8 +417,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true", help="serving rate sweep (separate JSON line)")
-    ap.add_argument("--rates", default="0.5,1,2,4")
-    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--rates", default="1,2,4")
+    ap.add_argument("--requests", type=int, default=16)
     ap.add_argument("--set", action="append", default=[], metavar="KEY=VALUE",
                     help="override a workload field (profiling cases), e.g. --set K=10 --set M=19")
     args = ap.parse_args()

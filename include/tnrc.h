@@ -22,7 +22,9 @@
  *     control: it does not enter the Hamiltonian and its gradient is 0.
  *   - Slice k applies A(dt/2) B(dt) A(dt/2): A = the gates exp(-i tau h_b) of
  *     all even bonds, B = of all odd bonds, with
- *       h_b = (g_b + gfix_b + J_b) ZZ + wL (x_b X + y_b Y) (x) I + wR I (x) (x_{b+1} X + y_{b+1} Y),
+ *       h_b = (g_b + gfix_b + J^z_b) ZZ + J^x_b XX + J^y_b YY
+ *             + wL (x_b X + y_b Y) (x) I + wR I (x) (x_{b+1} X + y_{b+1} Y),
+ *     (J^x = J^y = 0 unless crosstalk_terms = 3),
  *     wL = 1 on bond 0 else 1/2, wR = 1 on bond N-2 else 1/2.
  *   - Truncation: after every two-site gate keep the
  *     k = min(chi_max, #{sigma_i > max(sv_cutoff, 1e-13) sigma_1}) largest
@@ -86,6 +88,9 @@ typedef struct {
   int32_t warps_per_cta;         /* trajectory-kernel warps per CTA, 2..8; 0 = default      */
   int32_t ctas_per_sm;           /* resident trajectory CTAs per SM, 1..4 with
                                     warps_per_cta * ctas_per_sm <= 8; 0 = 1                */
+  int32_t crosstalk_terms;       /* 1 (or 0): J^z ZZ per bond, J[M][N-1]; 3: the Heisenberg
+                                    type J^x XX + J^y YY + J^z ZZ of Eq. Hp, J[M][N-1][3]
+                                    in the order (x, y, z)                                 */
 } tnrc_problem;
 
 /* Per-call statistics of the last tnrc_fidelity / tnrc_fidelity_grad. */
@@ -108,6 +113,10 @@ typedef struct {
   int64_t restarts;              /* trajectories of the last evaluation whose forward history
                                     did not fit their CTA's region packed and that were redone
                                     with checkpoints (results are identical either way)     */
+  int64_t phase_cycles[8];       /* SM cycles summed over warps per phase of the trajectory
+                                    kernel (contraction, Jacobi, rank/truncate, split,
+                                    environments, gradients, history copies, layer
+                                    barriers); zero unless built with TNRC_PHASE_TIMERS   */
 } tnrc_stats;
 
 /* Create a context on the current CUDA device, ordered on `cuda_stream`
@@ -122,15 +131,16 @@ tnrc_status tnrc_create(const tnrc_problem* problem, const tnrc_mps* inputs,
 /* Copy the controls u[K][C][N] (host, len = K*C*N doubles) to the device. */
 tnrc_status tnrc_set_controls(tnrc_ctx* ctx, const double* u, int64_t len);
 
-/* Draw J[M][N-1] on the device from the counter-based SplitMix64 stream of
- * `seed`: dist 0 = uniform on [-scale, scale] (Sec. II), 1 = normal N(0, scale^2)
- * by Box-Muller (sample s, bond b uses counter s*(N-1)+b, or 2x that and 2x+1). */
+/* Draw J on the device from the counter-based SplitMix64 stream of `seed`:
+ * dist 0 = uniform on [-scale, scale] (Sec. II), 1 = normal N(0, scale^2) by
+ * Box-Muller.  Entry i of the flattened J[M][N-1] (or J[M][N-1][3]) uses
+ * counter i (uniform) or counters 2i and 2i+1 (normal). */
 tnrc_status tnrc_sample_noise(tnrc_ctx* ctx, uint64_t seed, int32_t dist, double scale);
 
-/* Set J[M][N-1] explicitly (host, len = M*(N-1) doubles). */
+/* Set J explicitly (host, len = M*(N-1)*crosstalk_terms doubles). */
 tnrc_status tnrc_set_noise(tnrc_ctx* ctx, const double* J, int64_t len);
 
-/* Copy the current J[M][N-1] to the host (len = M*(N-1) doubles).
+/* Copy the current J to the host (len = M*(N-1)*crosstalk_terms doubles).
  * Errors: TNRC_E_STATE if no noise was set or sampled yet. */
 tnrc_status tnrc_get_noise(tnrc_ctx* ctx, double* J, int64_t len);
 
@@ -157,6 +167,15 @@ tnrc_status tnrc_get_stats(tnrc_ctx* ctx, tnrc_stats* stats);
  * call (tnrc_sync). */
 tnrc_status tnrc_set_controls_dev(tnrc_ctx* ctx, const double* d_u);
 tnrc_status tnrc_evaluate_dev(tnrc_ctx* ctx, double* d_F, double* d_grad, double* d_per_traj);
+/* Run tnrc_evaluate_dev through CUDA graphs (enable = 1) or plain launches
+ * (0, the default).  A graph is captured on the first call for each set of
+ * output pointers (and each of "gates rebuilt" / "gates current") and replayed
+ * on later calls; the trajectory-kernel timing of tnrc_get_stats does not
+ * count graph replays.  The first evaluation of a context must not be inside
+ * an application's own stream capture.  Errors: TNRC_E_INVALID when enabling
+ * on a context created on the legacy default stream (it cannot be captured). */
+tnrc_status tnrc_set_graphs(tnrc_ctx* ctx, int32_t enable);
+
 /* Synchronise the context's stream and report any device-side error flag. */
 tnrc_status tnrc_sync(tnrc_ctx* ctx);
 
@@ -170,7 +189,7 @@ tnrc_status tnrc_sync(tnrc_ctx* ctx);
  * carved from one static device array of 32 MiB compiled into the library,
  * which every GPU that loads the library holds until the process exits.
  *   problem, inputs[P], targets[P]: as for tnrc_create (host pointers);
- *   u[K][C][N], J[M][N-1]: host controls and noise;
+ *   u[K][C][N], J[M][N-1] (x crosstalk_terms): host controls and noise;
  *   cuda_stream: cudaStream_t the work is ordered on (NULL = legacy default);
  *   F, per_traj (nullable): host outputs, written only on TNRC_OK.
  * Synchronous at return.  Returns TNRC_E_TOO_LARGE when the problem's buffers
@@ -189,6 +208,18 @@ size_t tnrc_footprint(const tnrc_problem* problem);
 
 /* Release every resource of the context (NULL is accepted). */
 void tnrc_destroy(tnrc_ctx* ctx);
+
+/* Measure the current device's FP64 FMA throughput (GFLOP/s): 8 independent
+ * FMA chains per thread on 4 CTAs x 256 threads per SM, best of 2 timed
+ * launches after a warm-up, on the legacy default stream.  `scratch` is a
+ * device buffer of at least 4 * SMs * 256 doubles (written, not read).  The
+ * roofline denominator of the trajectory kernel, which is bound by FP64
+ * arithmetic (the paper has no counterpart; it quotes no hardware). */
+tnrc_status tnrc_measure_fp64_peak(void* scratch, size_t scratch_bytes, double* gflops);
+
+/* After TNRC_E_CUDA: which CUDA call failed and why ("" otherwise).  The
+ * string lives as long as the context. */
+const char* tnrc_last_error(const tnrc_ctx* ctx);
 
 /* Human-readable name of a status code. */
 const char* tnrc_status_string(tnrc_status status);

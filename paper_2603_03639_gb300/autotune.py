@@ -19,6 +19,7 @@ import sys
 import numpy as np
 
 CANDIDATES = [(8, 1), (6, 1), (5, 1), (4, 2), (4, 1), (3, 2), (2, 4)]
+QUICK = [(8, 1), (6, 1), (4, 2), (3, 2)]
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
 
@@ -38,8 +39,19 @@ def load(path=None):
 
 
 def lookup(N, K, chi, M, P, C, grad=True, path=None):
-    """(warps_per_cta, ctas_per_sm) cached for this shape, or (0, 0)."""
-    e = load(path).get(shape_key(N, K, chi, M, P, C, grad))
+    """(warps_per_cta, ctas_per_sm) cached for this shape -- or for the same
+    shape with the nearest ensemble-size bucket -- else (0, 0) (defaults)."""
+    cache = load(path)
+    key = shape_key(N, K, chi, M, P, C, grad)
+    e = cache.get(key)
+    if e is None:
+        head, tail = key.split("-T")
+        rest = tail.split("-", 1)[1]
+        t = int(tail.split("-", 1)[0])
+        near = [(abs(np.log2(int(k.split("-T")[1].split("-")[0])) - np.log2(t)), k) for k in cache
+                if k.startswith(head + "-T") and k.split("-T")[1].split("-", 1)[1] == rest]
+        if near:
+            e = cache[min(near)[1]]
     return (int(e["warps"]), int(e["ctas_per_sm"])) if e else (0, 0)
 
 
@@ -74,6 +86,7 @@ def main():
     ap.add_argument("--set", action="append", default=[], metavar="KEY=VALUE")
     ap.add_argument("--out", default=DEFAULT_CACHE)
     ap.add_argument("--fidelity-only", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="only the four usual winners")
     args = ap.parse_args()
     w = synth.WORKLOADS[args.workload]
     for kv in args.set:
@@ -82,7 +95,8 @@ def main():
     ins, tgs = w.states()
     grad = not args.fidelity_only
     best, times = tune(w.N, w.K, w.dt, w.chi, w.M, w.C, ins, tgs, w.controls(),
-                       (w.seed_J, w.noise_dist, w.noise_scale), mask=w.mask(), grad=grad)
+                       (w.seed_J, w.noise_dist, w.noise_scale), mask=w.mask(), grad=grad,
+                       candidates=QUICK if args.quick else CANDIDATES)
     cache = load(args.out)
     key = shape_key(w.N, w.K, w.chi, w.M, w.P, w.C, grad)
     cache[key] = {"warps": best[0], "ctas_per_sm": best[1], "workload": w.name,

@@ -36,8 +36,15 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
-def build(verbose=False, extra=()):
-    """Compile and link; returns the path of the shared library."""
+def build(verbose=False, extra=(), variant=""):
+    """Compile and link; returns the path of the shared library.  variant
+    "timers" builds lib/libtnrc_timers.so with the per-phase cycle counters."""
+    global BUILD, LIB
+    if variant == "timers":
+        extra = list(extra) + ["-DTNRC_PHASE_TIMERS"]
+        BUILD, LIB = os.path.join(HERE, "_build_timers"), os.path.join(LIBDIR, "libtnrc_timers.so")
+    else:
+        BUILD, LIB = os.path.join(HERE, "_build"), os.path.join(LIBDIR, "libtnrc.so")
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     srcs = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
@@ -58,4 +65,5 @@ def build(verbose=False, extra=()):
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, extra=["-Xptxas", "-v"] if "-v" in sys.argv else []))
+    print(build(verbose="-v" in sys.argv, extra=["-Xptxas", "-v"] if "-v" in sys.argv else [],
+                variant="timers" if "--timers" in sys.argv else ""))

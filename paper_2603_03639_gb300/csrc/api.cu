@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -13,8 +14,9 @@
 #include "tnrc_device.cuh"
 
 extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, size_t smem, cudaStream_t st);
+extern "C" cudaError_t tnrc_traj_prepare();
 extern "C" size_t tnrc_traj_smem(int warps, int slab_elems);
-extern "C" cudaError_t tnrc_launch_gates(int N, int K, int C, int M, double dt, const double* u,
+extern "C" cudaError_t tnrc_launch_gates(int N, int K, int C, int M, int terms, double dt, const double* u,
                                          const unsigned char* mask, const double* gfix, const double* J,
                                          tnrc::GateEntry* out, double2* merged, int* status, cudaStream_t st);
 extern "C" cudaError_t tnrc_launch_noise(unsigned long long seed, int dist, double scale, int M, int nb, double* J,
@@ -62,7 +64,7 @@ Layout make_layout(int N, int cap) {
 }
 
 struct Plan {
-  int N, K, C, chi, M, P, T;
+  int N, K, C, chi, M, P, T, terms;
   int seg, nseg;
   int warps, slab_elems;
   int grid;
@@ -85,6 +87,7 @@ bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, boo
   if (!(pb->dt > 0.0) || !std::isfinite(pb->dt) || !(pb->sv_cutoff >= 0.0) || !(pb->sv_cutoff < 1.0)) return false;
   if (pb->n_samples < 1 || pb->n_inputs < 1 || (pb->n_controls != 2 && pb->n_controls != 3)) return false;
   if (pb->checkpoint_every < 0) return false;
+  if (pb->crosstalk_terms != 0 && pb->crosstalk_terms != 1 && pb->crosstalk_terms != 3) return false;
   const long long T = (long long)pb->n_samples * pb->n_inputs;
   if (T > (1ll << 30)) return false;
   P.N = N;
@@ -94,6 +97,7 @@ bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, boo
   P.M = pb->n_samples;
   P.P = pb->n_inputs;
   P.T = (int)T;
+  P.terms = pb->crosstalk_terms == 3 ? 3 : 1;
   // checkpoint segments in truncated layers (2K+1 of them; 2 per slice)
   const int L = 2 * K + 1;
   P.seg = pb->checkpoint_every > 0 ? std::min(2 * pb->checkpoint_every, L) : (int)std::ceil(std::sqrt((double)L));
@@ -116,7 +120,15 @@ bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, boo
   }
   // the register file holds 8 warps of this kernel per SM
   const int ctas_per_sm = std::max(1, std::min(pb->ctas_per_sm > 0 ? pb->ctas_per_sm : 1, tnrc::kWarps / P.warps));
-  P.slab_elems = std::min(1024, 4 * chi * chi);
+  // each warp's shared slab holds theta^dagger up to slab_elems complex values
+  // (wider thetas use global scratch): split what the resident CTAs of an SM
+  // leave after the per-warp arrays, within the 227 KB a CTA may use
+  {
+    const int per_sm = 220 * 1024 / ctas_per_sm;
+    const int small = P.warps * (tnrc::kMaxDim * 12 + 64 * 16) + 1024;
+    const int per_warp = std::max(0, per_sm - small) / P.warps / 16;
+    P.slab_elems = std::max(256, std::min(4 * chi * chi, per_warp / 32 * 32));
+  }
   const int64_t cc = (int64_t)chi * chi;
   P.scratch_elems = 16 * cc;
   P.env_elems = 2 * (int64_t)(N + 1) * cc;
@@ -138,7 +150,7 @@ bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, boo
   P.off_u = take(KCN * 8);
   P.off_mask = take((int64_t)P.C * N);
   P.off_gfix = take((int64_t)K * (N - 1) * 8);
-  P.off_J = take((int64_t)P.M * (N - 1) * 8);
+  P.off_J = take((int64_t)P.M * (N - 1) * P.terms * 8);
   P.off_gates = take((int64_t)P.M * K * (N - 1) * sizeof(tnrc::GateEntry));
   P.off_merged = take((int64_t)P.M * std::max(K - 1, 1) * (N - 1) * 16 * 16);
   P.off_in = take((int64_t)P.P * P.L.bytes);
@@ -193,6 +205,16 @@ struct tnrc_ctx {
   // dimensions in each CTA's work region when it fits (else checkpoints)
   int packed_history = 1;
   long long history_cap = (long long)1 << 62;
+  // CUDA graphs of tnrc_evaluate_dev, one per (gradient?, outputs, gate rebuild?)
+  struct GraphEntry {
+    bool grad, gates;
+    double *dF, *dgrad, *dper;
+    cudaGraphExec_t exec;
+  };
+  bool use_graphs = false;
+  bool timed_last = false;        // ev0/ev1 bracket the last evaluation (not a graph replay)
+  std::vector<GraphEntry> graphs;
+  char err[256] = {0};            // the CUDA failure that made the context unusable
   tnrc_stats stats{};
   int n_sm = 0;
   template <class T>
@@ -203,22 +225,28 @@ struct tnrc_ctx {
 
 namespace {
 
-tnrc_status fail_cuda(tnrc_ctx* c) {
-  if (c) c->broken = true;
+tnrc_status fail_cuda(tnrc_ctx* c, cudaError_t e, int line) {
+  if (c) {
+    c->broken = true;
+    snprintf(c->err, sizeof(c->err), "api.cu:%d: %s: %s", line, cudaGetErrorName(e), cudaGetErrorString(e));
+  }
   return TNRC_E_CUDA;
 }
 
-#define CK(x)                               \
-  do {                                      \
-    if ((x) != cudaSuccess) return fail_cuda(ctx); \
+#define CK(x)                                                   \
+  do {                                                          \
+    const cudaError_t ck_e_ = (x);                              \
+    if (ck_e_ != cudaSuccess) return fail_cuda(ctx, ck_e_, __LINE__); \
   } while (0)
 
-tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, double* dper) {
+tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, double* dper, bool capturing = false) {
   Plan& P = ctx->plan;
   cudaStream_t st = ctx->stream;
-  CK(cudaEventRecord(ctx->ev0, st));
+  if (!capturing) CK(cudaEventRecord(ctx->ev0, st));
+  ctx->timed_last = !capturing;
   if (ctx->gates_dirty) {
-    CK(tnrc_launch_gates(P.N, P.K, P.C, P.M, ctx->dt, ctx->at<double>(P.off_u), ctx->at<unsigned char>(P.off_mask),
+    CK(tnrc_launch_gates(P.N, P.K, P.C, P.M, P.terms, ctx->dt, ctx->at<double>(P.off_u),
+                         ctx->at<unsigned char>(P.off_mask),
                          ctx->at<double>(P.off_gfix), ctx->at<double>(P.off_J),
                          ctx->at<tnrc::GateEntry>(P.off_gates), ctx->at<double2>(P.off_merged),
                          ctx->at<int>(P.off_status), st));
@@ -263,7 +291,7 @@ tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, dou
   tp.status = ctx->at<int>(P.off_status);
   tp.work_counter = ctx->at<int>(P.off_wc);
   const size_t smem = tnrc_traj_smem(P.warps, P.slab_elems);
-  const bool timed = ctx->tev_used + 2 <= ctx->tev.size();
+  const bool timed = !capturing && ctx->tev_used + 2 <= ctx->tev.size();
   if (timed) CK(cudaEventRecord(ctx->tev[ctx->tev_used], st));
   CK(tnrc_launch_traj(&tp, P.grid, smem, st));
   if (timed) {
@@ -274,7 +302,36 @@ tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, dou
   CK(tnrc_launch_reduce(ctx->at<double2>(P.off_O), P.T, dF ? dF : ctx->at<double>(P.off_F), dper,
                         grad ? ctx->at<double>(P.off_gsp) : nullptr, X,
                         grad ? (dgrad ? dgrad : ctx->at<double>(P.off_grad)) : nullptr, st));
-  CK(cudaEventRecord(ctx->ev1, st));
+  if (!capturing) CK(cudaEventRecord(ctx->ev1, st));
+  return TNRC_OK;
+}
+
+// tnrc_evaluate_dev through a CUDA graph captured on first use for these
+// outputs and replayed afterwards (the launch sequence and every kernel
+// argument are fixed per context, so a replay is the same work).
+tnrc_status launch_eval_graph(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, double* dper) {
+  const bool gates = ctx->gates_dirty;
+  for (auto& g : ctx->graphs) {
+    if (g.grad == grad && g.gates == gates && g.dF == dF && g.dgrad == dgrad && g.dper == dper) {
+      CK(cudaGraphLaunch(g.exec, ctx->stream));
+      ctx->gates_dirty = false;
+      ctx->timed_last = false;
+      return TNRC_OK;
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  const tnrc_status s = launch_eval(ctx, grad, dF, dgrad, dper, true);
+  const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+  if (s != TNRC_OK) return s;
+  CK(e);
+  tnrc_ctx::GraphEntry g{grad, gates, dF, dgrad, dper, nullptr};
+  const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CK(ei);
+  ctx->graphs.push_back(g);
+  CK(cudaGraphLaunch(g.exec, ctx->stream));
+  ctx->timed_last = false;
   return TNRC_OK;
 }
 
@@ -288,7 +345,8 @@ tnrc_status finish(tnrc_ctx* ctx) {
     return TNRC_E_NUMERIC;
   }
   float ms = 0.f;
-  if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) == cudaSuccess) ctx->stats.last_ms = ms;
+  if (ctx->timed_last) CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+  ctx->stats.last_ms = ctx->timed_last ? ms : 0.0;
   return TNRC_OK;
 }
 
@@ -367,6 +425,7 @@ tnrc_status tnrc_create(const tnrc_problem* pb, const tnrc_mps* inputs, const tn
   };
   if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess)
     return bail(TNRC_E_CUDA);
+  if (tnrc_traj_prepare() != cudaSuccess) return bail(TNRC_E_CUDA);
   ctx->tev.assign(512, nullptr);
   for (auto& e : ctx->tev)
     if (cudaEventCreate(&e) != cudaSuccess) return bail(TNRC_E_CUDA);
@@ -494,7 +553,7 @@ tnrc_status tnrc_sample_noise(tnrc_ctx* ctx, uint64_t seed, int32_t dist, double
   if (!ctx || (dist != 0 && dist != 1) || !(scale >= 0.0) || !std::isfinite(scale)) return TNRC_E_INVALID;
   if (ctx->broken) return TNRC_E_CUDA;
   const Plan& P = ctx->plan;
-  CK(tnrc_launch_noise(seed, dist, scale, P.M, P.N - 1, ctx->at<double>(P.off_J), ctx->stream));
+  CK(tnrc_launch_noise(seed, dist, scale, P.M, (P.N - 1) * P.terms, ctx->at<double>(P.off_J), ctx->stream));
   ctx->have_J = true;
   ctx->gates_dirty = true;
   return TNRC_OK;
@@ -504,7 +563,7 @@ tnrc_status tnrc_set_noise(tnrc_ctx* ctx, const double* J, int64_t len) {
   if (!ctx || !J) return TNRC_E_INVALID;
   if (ctx->broken) return TNRC_E_CUDA;
   const Plan& P = ctx->plan;
-  if (len != (int64_t)P.M * (P.N - 1)) return TNRC_E_INVALID;
+  if (len != (int64_t)P.M * (P.N - 1) * P.terms) return TNRC_E_INVALID;
   for (int64_t i = 0; i < len; ++i)
     if (!std::isfinite(J[i])) return TNRC_E_INVALID;
   CK(cudaMemcpyAsync(ctx->at<void>(P.off_J), J, (size_t)len * 8, cudaMemcpyHostToDevice, ctx->stream));
@@ -519,7 +578,7 @@ tnrc_status tnrc_get_noise(tnrc_ctx* ctx, double* J, int64_t len) {
   if (ctx->broken) return TNRC_E_CUDA;
   if (!ctx->have_J) return TNRC_E_STATE;
   const Plan& P = ctx->plan;
-  if (len != (int64_t)P.M * (P.N - 1)) return TNRC_E_INVALID;
+  if (len != (int64_t)P.M * (P.N - 1) * P.terms) return TNRC_E_INVALID;
   CK(cudaStreamSynchronize(ctx->stream));
   CK(cudaMemcpy(J, ctx->at<void>(P.off_J), (size_t)len * 8, cudaMemcpyDeviceToHost));
   return TNRC_OK;
@@ -537,7 +596,16 @@ tnrc_status tnrc_evaluate_dev(tnrc_ctx* ctx, double* d_F, double* d_grad, double
   if (!ctx || !d_F) return TNRC_E_INVALID;
   if (ctx->broken) return TNRC_E_CUDA;
   if (!ctx->have_u || !ctx->have_J) return TNRC_E_STATE;
+  if (ctx->use_graphs) return launch_eval_graph(ctx, d_grad != nullptr, d_F, d_grad, d_per_traj);
   return launch_eval(ctx, d_grad != nullptr, d_F, d_grad, d_per_traj);
+}
+
+tnrc_status tnrc_set_graphs(tnrc_ctx* ctx, int32_t enable) {
+  if (!ctx || (enable != 0 && enable != 1)) return TNRC_E_INVALID;
+  if (ctx->broken) return TNRC_E_CUDA;
+  if (enable && ctx->stream == nullptr) return TNRC_E_INVALID;  // the legacy stream cannot be captured
+  ctx->use_graphs = enable != 0;
+  return TNRC_OK;
 }
 
 tnrc_status tnrc_sync(tnrc_ctx* ctx) {
@@ -573,6 +641,7 @@ tnrc_status tnrc_get_stats(tnrc_ctx* ctx, tnrc_stats* stats) {
   for (int d = 0; d <= P.chi; ++d) s.bond_hist[d] = (int64_t)c[5 + d];
   s.alg_flops = (double)c[3];
   s.restarts = (int64_t)c[4];
+  for (int i = 0; i < tnrc::kNumPhases; ++i) s.phase_cycles[i] = (int64_t)c[tnrc::kCtrPhase + i];
   double tms = 0.0;
   for (size_t i = 0; i + 1 < ctx->tev_used; i += 2) {
     float ms = 0.f;
@@ -599,7 +668,13 @@ void tnrc_destroy(tnrc_ctx* ctx) {
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   for (auto e : ctx->tev)
     if (e) cudaEventDestroy(e);
+  for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
   delete ctx;
+}
+
+const char* tnrc_last_error(const tnrc_ctx* ctx) {
+  if (!ctx) return "";
+  return ctx->err;
 }
 
 const char* tnrc_status_string(tnrc_status s) {

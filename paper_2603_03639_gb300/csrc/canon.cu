@@ -172,6 +172,7 @@ __global__ void canon_kernel(CanonArgs a) {
 }  // namespace tnrc
 
 extern "C" cudaError_t tnrc_launch_canon(const tnrc::CanonArgs* a, int nmps, cudaStream_t st) {
+  (void)cudaGetLastError();  // report only this launch below
   tnrc::canon_kernel<<<nmps, 32, 0, st>>>(*a);
   return cudaGetLastError();
 }

@@ -3,7 +3,8 @@
 // gate_kernel: one thread per (sample s, slice k, bond b).  Builds the bond
 // Hamiltonian of Eq. sysH with ZZ crosstalk,
 //   h = c ZZ + wL (x_b X + y_b Y) (x) I + wR I (x) (x_{b+1} X + y_{b+1} Y),
-//   c = g_b (if a control) + gfix_{k,b} + J^(s)_b,
+//   c = g_b (if a control) + gfix_{k,b} + J^z(s)_b, plus J^x XX + J^y YY for
+//   the Heisenberg-type crosstalk of Eq. Hp,
 // diagonalises it by cyclic complex Jacobi rotations (FP64), and stores
 //   G = V e^{-i tau Lam} V^dag            (tau = dt/2 on even bonds, dt on odd)
 //   Gam_jk = -i tau e^{-i tau (l_j + l_k)/2} sinc(tau (l_j - l_k)/2)
@@ -68,12 +69,12 @@ __device__ __forceinline__ void herm_rotate(double2 (&h)[16], double2 (&V)[16], 
 }
 
 struct GateArgs {
-  int N, K, C, M;
+  int N, K, C, M, terms;
   double dt;
   const double* u;            // [K][C][N]
   const unsigned char* mask;  // [C][N]
   const double* gfix;         // [K][N-1] or null
-  const double* J;            // [M][N-1]
+  const double* J;            // [M][N-1][terms]: (J^z) or (J^x, J^y, J^z)
   GateEntry* out;             // [M][K][N-1]
   int* status;
 };
@@ -92,7 +93,10 @@ __global__ void gate_kernel(GateArgs a) {
   const double yl = uk[a.N + b] * mk[a.N + b];
   const double xr = uk[b + 1] * mk[b + 1];
   const double yr = uk[a.N + b + 1] * mk[a.N + b + 1];
-  double c = a.J[(size_t)s * nb + b];
+  const double* Jb = a.J + ((size_t)s * nb + b) * a.terms;
+  double c = Jb[a.terms - 1];
+  const double jx = (a.terms == 3) ? Jb[0] : 0.0;
+  const double jy = (a.terms == 3) ? Jb[1] : 0.0;
   if (a.C == 3) c += uk[2 * a.N + b] * mk[2 * a.N + b];
   if (a.gfix) c += a.gfix[(size_t)k * nb + b];
   const double wl = (b == 0) ? 1.0 : 0.5;
@@ -121,6 +125,11 @@ __global__ void gate_kernel(GateArgs a) {
     h[(2 * s1) * 4 + (2 * s1 + 1)] = rz;
     h[(2 * s1 + 1) * 4 + (2 * s1)] = cconj(rz);
   }
+  // crosstalk J^x XX + J^y YY: <00|.|11> = jx - jy, <01|.|10> = jx + jy
+  h[0 * 4 + 3].x += jx - jy;
+  h[3 * 4 + 0].x += jx - jy;
+  h[1 * 4 + 2].x += jx + jy;
+  h[2 * 4 + 1].x += jx + jy;
   double scale2 = 0.0;
 #pragma unroll
   for (int i = 0; i < 16; ++i) scale2 += cabs2(h[i]);
@@ -245,13 +254,14 @@ __global__ void reduce_grad_kernel(const double* gsp, int T, int X, double* grad
 
 }  // namespace tnrc
 
-extern "C" cudaError_t tnrc_launch_gates(int N, int K, int C, int M, double dt, const double* u,
+extern "C" cudaError_t tnrc_launch_gates(int N, int K, int C, int M, int terms, double dt, const double* u,
                                          const unsigned char* mask, const double* gfix, const double* J,
                                          tnrc::GateEntry* out, double2* merged, int* status, cudaStream_t st) {
-  tnrc::GateArgs a{N, K, C, M, dt, u, mask, gfix, J, out, status};
+  tnrc::GateArgs a{N, K, C, M, terms, dt, u, mask, gfix, J, out, status};
   const long long total = (long long)M * K * (N - 1);
   const int threads = 128;
   const long long blocks = (total + threads - 1) / threads;
+  (void)cudaGetLastError();  // report only this launch below
   tnrc::gate_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);
   if (K > 1) {
     const long long tm = (long long)M * (K - 1) * (N / 2) * 16;
@@ -264,12 +274,14 @@ extern "C" cudaError_t tnrc_launch_noise(unsigned long long seed, int dist, doub
                                          cudaStream_t st) {
   const long long total = (long long)M * nb;
   const int threads = 256;
+  (void)cudaGetLastError();  // report only this launch below
   tnrc::noise_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(seed, dist, scale, M, nb, J);
   return cudaGetLastError();
 }
 
 extern "C" cudaError_t tnrc_launch_reduce(const double2* O, int T, double* F, double* per_traj, const double* gsp,
                                           int X, double* grad, cudaStream_t st) {
+  (void)cudaGetLastError();  // report only this launch below
   tnrc::reduce_fidelity_kernel<<<1, 256, 0, st>>>(O, T, F, per_traj);
   if (gsp && grad) tnrc::reduce_grad_kernel<<<(X + 127) / 128, 128, 0, st>>>(gsp, T, X, grad);
   return cudaGetLastError();

@@ -29,8 +29,9 @@
 #include "tnrc_device.cuh"
 
 extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, size_t smem, cudaStream_t st);
+extern "C" cudaError_t tnrc_traj_prepare();
 extern "C" size_t tnrc_traj_smem(int warps, int slab_elems);
-extern "C" cudaError_t tnrc_launch_gates(int N, int K, int C, int M, double dt, const double* u,
+extern "C" cudaError_t tnrc_launch_gates(int N, int K, int C, int M, int terms, double dt, const double* u,
                                          const unsigned char* mask, const double* gfix, const double* J,
                                          tnrc::GateEntry* out, double2* merged, int* status, cudaStream_t st);
 extern "C" cudaError_t tnrc_launch_reduce(const double2* O, int T, double* F, double* per_traj, const double* gsp,
@@ -79,6 +80,8 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
             C = pb->n_controls;
   if (N < 2 || N > 256 || K < 1 || chi < 1 || chi > tnrc::kMaxChi || M < 1 || P < 1 || (C != 2 && C != 3))
     return TNRC_E_INVALID;
+  if (pb->crosstalk_terms != 0 && pb->crosstalk_terms != 1 && pb->crosstalk_terms != 3) return TNRC_E_INVALID;
+  const int terms = pb->crosstalk_terms == 3 ? 3 : 1;
   if (!(pb->dt > 0.0) || !std::isfinite(pb->dt) || !(pb->sv_cutoff >= 0.0) || !(pb->sv_cutoff < 1.0))
     return TNRC_E_INVALID;
   const long long T = (long long)M * P;
@@ -97,7 +100,7 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   const int64_t KCN = (int64_t)K * C * N;
   for (int64_t i = 0; i < KCN; ++i)
     if (!std::isfinite(u[i])) return TNRC_E_INVALID;
-  for (int64_t i = 0; i < (int64_t)M * (N - 1); ++i)
+  for (int64_t i = 0; i < (int64_t)M * (N - 1) * terms; ++i)
     if (!std::isfinite(J[i])) return TNRC_E_INVALID;
 
   // ---- layout of one state slot (capacity D_i = min(2^i, 2^(N-i), chi)) ----
@@ -138,7 +141,7 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
     return o;
   };
   const int64_t o_mask = take((int64_t)C * N), o_gfix = take((int64_t)K * (N - 1) * 8), o_u = take(KCN * 8),
-                o_J = take((int64_t)M * (N - 1) * 8), o_site = take((int64_t)N * 4),
+                o_J = take((int64_t)M * (N - 1) * terms * 8), o_site = take((int64_t)N * 4),
                 o_dcap = take((int64_t)(N + 1) * 4),
                 o_rdims = take((int64_t)rdims.size() * 4), o_roffs = take((int64_t)roffs.size() * 8),
                 o_raw = take(rtotal * 16), o_cwork = take((int64_t)2 * P * cwork * 16),
@@ -193,7 +196,7 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   bool ok = cudaMemcpyAsync(base + o_mask, mask.data(), mask.size(), cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(base + o_gfix, gfix.data(), gfix.size() * 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(base + o_u, u, KCN * 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
-            cudaMemcpyAsync(base + o_J, J, (size_t)M * (N - 1) * 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+            cudaMemcpyAsync(base + o_J, J, (size_t)M * (N - 1) * terms * 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(base + o_site, site_off.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(base + o_dcap, dcap.data(), (size_t)(N + 1) * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(base + o_rdims, rdims.data(), rdims.size() * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
@@ -226,7 +229,7 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   ca.status = status;
   if (tnrc_launch_canon(&ca, 2 * P, st) != cudaSuccess) return TNRC_E_CUDA;
   // ---- gates ----
-  if (tnrc_launch_gates(N, K, C, M, pb->dt, reinterpret_cast<const double*>(base + o_u), base + o_mask,
+  if (tnrc_launch_gates(N, K, C, M, terms, pb->dt, reinterpret_cast<const double*>(base + o_u), base + o_mask,
                         reinterpret_cast<const double*>(base + o_gfix), reinterpret_cast<const double*>(base + o_J),
                         reinterpret_cast<tnrc::GateEntry*>(base + o_gates),
                         reinterpret_cast<double2*>(base + o_merged), status, st) != cudaSuccess)
@@ -268,6 +271,7 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   tp.counters = counters;
   tp.status = status;
   tp.work_counter = work_counter;
+  if (tnrc_traj_prepare() != cudaSuccess) return TNRC_E_CUDA;
   if (tnrc_launch_traj(&tp, grid, tnrc_traj_smem(warps, slab), st) != cudaSuccess) return TNRC_E_CUDA;
   if (tnrc_launch_reduce(tp.O, (int)T, dF, per_traj ? reinterpret_cast<double*>(base + o_per) : nullptr, nullptr, 0,
                          nullptr, st) != cudaSuccess)

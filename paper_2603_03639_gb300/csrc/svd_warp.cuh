@@ -68,16 +68,25 @@ __device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, int lan
         if (aa > thr && bb > thr && ab2 > tol2 * aa * bb) {
           rotated = 1;
           // Real rotation of the pair after the phase of <a,b> is divided out:
-          // zeta = (|b|^2 - |a|^2) / (2|<a,b>|), t = tan(theta) (smaller root).
+          // zeta = (|b|^2 - |a|^2) / (2|<a,b>|) = cot(2 theta).  With
+          // r = 1/sqrt(1 + zeta^2) = |sin 2theta| and q = |zeta| r = cos 2theta,
+          // c = sqrt((1 + q)/2) and s = sign(zeta) r / (2c): two reciprocal
+          // square roots, no cancellation, c^2 + s^2 = 1 to rounding.
           const double inv = rsqrt(ab2);
           const double zeta = (bb - aa) * 0.5 * inv;
-          double t;
-          if (fabs(zeta) > 1e150)
-            t = 0.5 / zeta;
-          else
-            t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-          const double c = rsqrt(fma(t, t, 1.0));
-          const double s = c * t;
+          const double az = fabs(zeta);
+          double r, q;
+          if (az > 1e150) {
+            r = 1.0 / az;
+            q = 1.0;
+          } else {
+            r = rsqrt(fma(zeta, zeta, 1.0));
+            q = az * r;
+          }
+          const double hq = 0.5 * (1.0 + q);
+          const double rc = rsqrt(hq);
+          const double c = hq * rc;
+          const double s = copysign(0.5 * r * rc, zeta);
           const double2 sp = make_double2(s * ab.x * inv, s * ab.y * inv);  // s e^{i phi}
           // a <- c a - conj(sp) b ;  b <- c b + sp a
           for (int row = lig; row < n; row += g) {

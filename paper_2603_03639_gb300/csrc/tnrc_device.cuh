@@ -25,7 +25,28 @@ constexpr double kJacobiZero = 5e-15;       // columns below this x ||theta||_F 
 constexpr int kStatusNoConverge = 1;
 constexpr int kStatusNaN = 2;
 constexpr int kStatusBadDims = 4;
-constexpr int kNumCounters = 5 + kMaxChi + 1;   // device counters of one evaluation
+constexpr int kCtrPhase = 5 + kMaxChi + 1;      // first of kNumPhases cycle counters
+constexpr int kNumPhases = 8;
+constexpr int kNumCounters = kCtrPhase + kNumPhases;   // device counters of one evaluation
+
+// Per-phase cycle counters (lane 0 of every warp, clock64), compiled in only
+// with -DTNRC_PHASE_TIMERS: 0 contraction, 1 Jacobi sweeps, 2 rank/truncate,
+// 3 split and write-back, 4 environment sweeps, 5 mixed densities and gate
+// gradients, 6 history and slot copies, 7 waiting at layer barriers.
+#ifdef TNRC_PHASE_TIMERS
+#define TNRC_TIC(v) const long long v = clock64()
+#define TNRC_TOC(w, idx, v) \
+  do {                      \
+    (w).ph[idx] += clock64() - (v); \
+  } while (0)
+#else
+#define TNRC_TIC(v) \
+  do {              \
+  } while (0)
+#define TNRC_TOC(w, idx, v) \
+  do {                      \
+  } while (0)
+#endif
 
 struct SlotLayout {
   int N, chi;

@@ -36,6 +36,9 @@ struct WarpCtx {
   double disc;
   int maxk;
   unsigned long long alg;   // algorithmic flops counted by lane 0
+  long long ph[kNumPhases]; // phase cycles (TNRC_PHASE_TIMERS builds)
+  int* order;               // shared, CTA-wide: bonds of the current layer by decreasing cost
+  int* next;                // shared, CTA-wide: next entry of `order` to take
 };
 
 // Algorithmic flops of one two-site update with theta of m x n (m = 2 Dl,
@@ -100,6 +103,7 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
     for (int c = 0; c < 4; ++c) g[r * 4 + c] = adjoint ? cconj(G[c * 4 + r]) : G[r * 4 + c];
 
   // Phase 1: Phi = G (B_b B_{b+1}) and theta^dagger (column (al s1), row (s2 ga)).
+  TNRC_TIC(t_c);
   double fro = 0.0;
   for (int it = lane; it < Dl * Dr; it += 32) {
     const int al = it / Dr, ga = it - al * Dr;
@@ -134,11 +138,15 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   }
   fro = warp_sum(fro);
   __syncwarp();
+  TNRC_TOC(w, 0, t_c);
 
   // Phase 2: one-sided Jacobi on the m columns of theta^dagger.
+  TNRC_TIC(t_j);
   const int sw = warp_jacobi(T, n, m, fro, lane);
+  TNRC_TOC(w, 1, t_j);
 
   // Phase 3: rank, truncate.
+  TNRC_TIC(t_r);
   double kept2, tot2;
   int k = warp_rank_truncate(T, n, m, chi, p.eps, w.sig2, w.perm, lane, kept2, tot2);
   if (k > Y.dcap[b + 1]) {  // cannot happen (k <= min(m, n, chi)); keeps memory in bounds regardless
@@ -158,8 +166,10 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   }
   if (count) w.alg += update_flops(m, n, Dc, k);
   const double inv_kn = rsqrt(kept2);
+  TNRC_TOC(w, 2, t_r);
 
   // Phase 4: write lam_b, B_{b+1} = Y_k^dag, B_b = Phi Y_k / |S_k|.
+  TNRC_TIC(t_w);
   double* lamw = lam + (size_t)b * lstride;
   for (int i = lane; i < k; i += 32) lamw[i] = sqrt(w.sig2[w.perm[i]]) * inv_kn;
   for (int it = lane; it < k * n; it += 32) {
@@ -179,6 +189,7 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   __syncwarp();
   if (lane == 0) D[b + 1] = k;
   __syncwarp();
+  TNRC_TOC(w, 3, t_w);
 }
 
 // ---------------------------------------------------------------------------
@@ -413,6 +424,7 @@ __device__ void layer_gradient(const TrajParams& p, const Lay& Y, const unsigned
   const int lane = w.lane;
 
   // left environments L_i (sites < i) for i <= N-2, right R_i (sites >= i) for i >= 2
+  TNRC_TIC(t_e);
   if (warp == 0) {
     if (lane == 0) Lbuf[0] = make_double2(1.0, 0.0);
     __syncwarp();
@@ -431,6 +443,8 @@ __device__ void layer_gradient(const TrajParams& p, const Lay& Y, const unsigned
     }
   }
   __syncthreads();
+  TNRC_TOC(w, 4, t_e);
+  TNRC_TIC(t_g);
 
   const int nb = (N - 1 - parity + 1) / 2;
   for (int j = warp; j < nb; j += p.warps) {
@@ -527,6 +541,7 @@ __device__ void layer_gradient(const TrajParams& p, const Lay& Y, const unsigned
     }
     __syncwarp();
   }
+  TNRC_TOC(w, 5, t_g);
   __syncthreads();
 }
 
@@ -561,15 +576,47 @@ __device__ int copy_slot(const TrajParams& p, const Lay& Ys, const unsigned char
   return 0;
 }
 
+// Cost of a two-site update with theta of (2 Dl) x (2 Dr): the Jacobi work
+// grows as m n min(m, n).
+__device__ __forceinline__ long long update_cost(int Dl, int Dr) {
+  const long long m = 2 * Dl, n = 2 * Dr;
+  return m * n * (m < n ? m : n);
+}
+
+// All bonds of truncated layer l.  The warps take bonds from a shared counter
+// in decreasing order of cost (largest SVD first), so that they reach the
+// layer barrier together; a bond's result does not depend on which warp
+// computes it.
 __device__ void apply_layer(const TrajParams& p, const Lay& Y, unsigned char* slot, int s, int l, bool adjoint,
-                           bool record, bool count, WarpCtx& w, int warp) {
+                            bool record, bool count, WarpCtx& w, int warp) {
   const int parity = l & 1;
   const int nb = (p.N - 1 - parity + 1) / 2;
-  for (int j = warp; j < nb; j += p.warps) {
-    const int b = parity + 2 * j;
-    two_site_update(p, Y, slot, b, layer_gate(p, s, l, b), adjoint, record, count, w);
+  const int lane = w.lane;
+  if (warp == 0) {
+    const int* D = slot_dims(slot);
+    for (int j = lane; j < nb; j += 32) {
+      const long long cj = update_cost(D[parity + 2 * j], D[parity + 2 * j + 2]);
+      int rk = 0;
+      for (int i = 0; i < nb; ++i) {
+        const long long ci = update_cost(D[parity + 2 * i], D[parity + 2 * i + 2]);
+        rk += (ci > cj || (ci == cj && i < j)) ? 1 : 0;
+      }
+      w.order[rk] = parity + 2 * j;
+    }
+    if (lane == 0) *w.next = 0;
   }
   __syncthreads();
+  for (;;) {
+    int j = 0;
+    if (lane == 0) j = atomicAdd(w.next, 1);
+    j = __shfl_sync(0xffffffffu, j, 0);
+    if (j >= nb) break;
+    const int b = w.order[j];
+    two_site_update(p, Y, slot, b, layer_gate(p, s, l, b), adjoint, record, count, w);
+  }
+  TNRC_TIC(t_b);
+  __syncthreads();
+  TNRC_TOC(w, 7, t_b);
 }
 
 // One trajectory (sample s, input pi) with the CTA's work region `base`.
@@ -605,7 +652,9 @@ __device__ int run_trajectory(const TrajParams& p, bool packed, unsigned char* b
       if (packed) {
         const size_t need = packed_bytes(slot_dims(a_slot), p.N);
         if (pos + need > hbytes) return 1;
+        TNRC_TIC(t_h);
         pack_state(p, Y, a_slot, harena + pos);
+        TNRC_TOC(w, 6, t_h);
         if (threadIdx.x == 0) hpos[l] = (long long)pos;
         pos += (need + 255) / 256 * 256;
       } else if (q == Y.nseg - 1) {
@@ -675,6 +724,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1) traj_kernel(TrajParams p) {
   __shared__ double s_disc[kWarps];
   __shared__ int s_maxk[kWarps];
   __shared__ double2 s_O;
+  __shared__ int s_order[128];
+  __shared__ int s_next;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   double2* slabs = reinterpret_cast<double2*>(smem_raw);
@@ -692,6 +743,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1) traj_kernel(TrajParams p) {
   w.sweeps = 0;
   w.updates = 0;
   w.alg = 0;
+  for (int i = 0; i < kNumPhases; ++i) w.ph[i] = 0;
+  w.order = s_order;
+  w.next = &s_next;
   unsigned char* base = p.work + (size_t)blockIdx.x * p.work_stride;
 
   for (;;) {
@@ -719,19 +773,29 @@ __global__ void __launch_bounds__(kWarps * 32, 1) traj_kernel(TrajParams p) {
     atomicAdd(&p.counters[0], (unsigned long long)w.updates);
     atomicAdd(&p.counters[1], (unsigned long long)w.sweeps);
     atomicAdd(&p.counters[3], w.alg);
+#ifdef TNRC_PHASE_TIMERS
+    for (int i = 0; i < kNumPhases; ++i) atomicAdd(&p.counters[kCtrPhase + i], (unsigned long long)w.ph[i]);
+#endif
   }
 }
 
 }  // namespace tnrc
 
-// host-side launcher
+// host-side launcher; the shared-memory limit is raised once per device and
+// process (tnrc_create calls tnrc_traj_prepare before any launch or capture)
+extern "C" cudaError_t tnrc_traj_prepare() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static bool attr_set[64] = {false};
+  if (dev >= 0 && dev < 64 && attr_set[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(tnrc::traj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) attr_set[dev] = true;
+  return e;
+}
+
 extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, size_t smem, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tnrc::traj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  (void)cudaGetLastError();  // report only this launch below
   tnrc::traj_kernel<<<grid, p->warps * 32, smem, st>>>(*p);
   return cudaGetLastError();
 }

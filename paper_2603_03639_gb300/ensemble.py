@@ -15,10 +15,11 @@ _GAMMA = 0x9E3779B97F4A7C15
 _MASK = (1 << 64) - 1
 
 
-def shard_seed(seed: int, rank: int, m_local: int, n_sites: int, dist: int) -> int:
-    """Seed whose J[M_local][N-1] draw equals rows rank*m_local .. of the
-    global J drawn from ``seed`` (uniform: one counter per bond; normal: two)."""
-    per_sample = (n_sites - 1) * (1 if dist == 0 else 2)
+def shard_seed(seed: int, rank: int, m_local: int, n_sites: int, dist: int, terms: int = 1) -> int:
+    """Seed whose J[M_local][N-1](x terms) draw equals rows rank*m_local .. of
+    the global J drawn from ``seed`` (uniform: one counter per entry; normal:
+    two)."""
+    per_sample = (n_sites - 1) * terms * (1 if dist == 0 else 2)
     return (seed + rank * m_local * per_sample * _GAMMA) & _MASK
 
 

@@ -85,6 +85,7 @@ class _Slot:
         self.stream = torch.cuda.Stream(device=device)
         self.ctx = Context(req.N, req.K, req.dt, req.chi, req.M, req.C, req.inputs, req.targets,
                            cutoff=req.cutoff, mask=req.mask, stream=self.stream.cuda_stream)
+        self.ctx.set_graphs(True)   # each request replays the context's captured evaluation
         self.bytes = req.footprint()
         self.F = torch.zeros(1, dtype=torch.float64, device=device)
         self.g = torch.zeros((req.K, req.C, req.N), dtype=torch.float64, device=device)
@@ -146,7 +147,7 @@ class Server:
             self.cv.notify()
         return req
 
-    def drain(self, timeout: float = 3600.0):
+    def drain(self, timeout: float = 600.0):
         """Wait until every submitted request has finished."""
         t0 = time.perf_counter()
         with self.cv:
@@ -204,16 +205,33 @@ class Server:
                 if self.stop:
                     return
                 # complete finished requests
-                for s in self.slots:
+                for s in list(self.slots):
                     if s.busy is not None and s.event.query():
-                        req = s.collect()
+                        req = s.busy
+                        try:
+                            s.collect()
+                        except Exception as e:  # the context is unusable: drop it, fail the request
+                            req.error = "evaluation failed: %s" % e
+                            s.busy = None
+                            self.slots.remove(s)
                         req.finish = time.perf_counter()
                         s.last_used = req.finish
                         self.done.append(req)
                 # admit in arrival order while slots and memory allow
                 inflight = sum(1 for s in self.slots if s.busy is not None)
                 while self.pending and inflight < self.max_inflight:
-                    if not self._admit(self.pending[0]):
+                    try:
+                        admitted = self._admit(self.pending[0])
+                    except Exception as e:  # creation or launch failed: fail this request only
+                        req = self.pending[0]
+                        req.error = "admission failed: %s" % e
+                        req.finish = time.perf_counter()
+                        self.done.append(req)
+                        for s in [s for s in self.slots if s.busy is req]:
+                            s.busy = None
+                            self.slots.remove(s)
+                        admitted = True
+                    if not admitted:
                         break
                     self.pending.popleft()
                     inflight = sum(1 for s in self.slots if s.busy is not None)

@@ -10,7 +10,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "lib", "libtnrc.so")
+LIB_PATH = os.environ.get("TNRC_LIB") or os.path.join(_HERE, "lib", "libtnrc.so")
 
 TNRC_OK = 0
 STATUS_NAMES = {0: "TNRC_OK", -1: "TNRC_E_INVALID", -2: "TNRC_E_NOMEM", -3: "TNRC_E_CUDA",
@@ -21,13 +21,13 @@ EXPORTS = ("tnrc_create", "tnrc_set_controls", "tnrc_sample_noise", "tnrc_set_no
            "tnrc_fidelity",
            "tnrc_fidelity_grad", "tnrc_get_overlaps", "tnrc_get_stats", "tnrc_set_controls_dev",
            "tnrc_evaluate_dev", "tnrc_sync", "tnrc_footprint", "tnrc_destroy", "tnrc_status_string",
-           "tnrc_fidelity_static")
+           "tnrc_fidelity_static", "tnrc_set_graphs", "tnrc_last_error", "tnrc_measure_fp64_peak")
 
 
 class TNRCError(RuntimeError):
-    def __init__(self, status: int, where: str):
+    def __init__(self, status: int, where: str, detail: str = ""):
         self.status = status
-        super().__init__("%s failed: %s" % (where, _status_string(status)))
+        super().__init__("%s failed: %s%s" % (where, _status_string(status), (" (%s)" % detail) if detail else ""))
 
 
 class Problem(ctypes.Structure):
@@ -36,7 +36,7 @@ class Problem(ctypes.Structure):
                 ("n_samples", ctypes.c_int32), ("n_controls", ctypes.c_int32), ("n_inputs", ctypes.c_int32),
                 ("control_mask", ctypes.POINTER(ctypes.c_uint8)), ("g_fixed", ctypes.POINTER(ctypes.c_double)),
                 ("checkpoint_every", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("crosstalk_terms", ctypes.c_int32)]
 
 
 class MPSDesc(ctypes.Structure):
@@ -49,8 +49,11 @@ class Stats(ctypes.Structure):
                 ("hist_len", ctypes.c_int32), ("bond_hist", ctypes.c_int64 * 65),
                 ("discarded_weight", ctypes.c_double), ("last_ms", ctypes.c_double),
                 ("alg_flops", ctypes.c_double), ("traj_ms", ctypes.c_double), ("traj_launches", ctypes.c_int64),
-                ("restarts", ctypes.c_int64)]
+                ("restarts", ctypes.c_int64), ("phase_cycles", ctypes.c_int64 * 8)]
 
+
+#: trajectory-kernel phases of tnrc_stats.phase_cycles
+PHASES = ("contraction", "jacobi", "truncate", "split", "environments", "gradients", "history", "barriers")
 
 _LIB = None
 
@@ -77,6 +80,12 @@ def lib() -> ctypes.CDLL:
         L.tnrc_set_controls_dev.argtypes = [vp, vp]
         L.tnrc_evaluate_dev.argtypes = [vp, vp, vp, vp]
         L.tnrc_sync.argtypes = [vp]
+        L.tnrc_measure_fp64_peak.argtypes = [vp, ctypes.c_size_t, dp]
+        L.tnrc_measure_fp64_peak.restype = i32
+        L.tnrc_last_error.argtypes = [vp]
+        L.tnrc_last_error.restype = ctypes.c_char_p
+        L.tnrc_set_graphs.argtypes = [vp, i32]
+        L.tnrc_set_graphs.restype = i32
         L.tnrc_footprint.argtypes = [ctypes.POINTER(Problem)]
         L.tnrc_footprint.restype = ctypes.c_size_t
         L.tnrc_destroy.argtypes = [vp]
@@ -102,9 +111,12 @@ def _status_string(s: int) -> str:
         return STATUS_NAMES.get(s, str(s))
 
 
-def _check(s: int, where: str):
+def _check(s: int, where: str, handle=None):
     if s != TNRC_OK:
-        raise TNRCError(s, where)
+        detail = ""
+        if s == -3 and handle is not None and handle.value:
+            detail = lib().tnrc_last_error(handle).decode(errors="replace")
+        raise TNRCError(s, where, detail)
 
 
 def _dp(a: np.ndarray):
@@ -121,7 +133,7 @@ def _pack(state):
 
 
 def make_problem(N, K, dt, chi, M, C, P, cutoff=1e-12, mask=None, g_fixed=None, checkpoint_every=0, warps=0,
-                 ctas_per_sm=0):
+                 ctas_per_sm=0, crosstalk=1):
     """A ``Problem`` plus the arrays it points to (keep both alive)."""
     keep = []
     pb = Problem()
@@ -139,6 +151,7 @@ def make_problem(N, K, dt, chi, M, C, P, cutoff=1e-12, mask=None, g_fixed=None, 
     pb.checkpoint_every = checkpoint_every
     pb.warps_per_cta = warps
     pb.ctas_per_sm = ctas_per_sm
+    pb.crosstalk_terms = crosstalk
     return pb, keep
 
 
@@ -153,14 +166,14 @@ def _descs(states):
 
 
 def fidelity_static(N, K, dt, chi, C, inputs, targets, u, J, cutoff=1e-12, mask=None, g_fixed=None,
-                    stream=None, per_traj=False):
+                    stream=None, per_traj=False, crosstalk=1):
     """F (and per-trajectory |O|^2) through tnrc_fidelity_static, which
     allocates no device memory: for callers that cannot call cudaMalloc.
     Calls must not overlap on the GPU (they share one static array)."""
     J = np.ascontiguousarray(J, dtype=np.float64)
     u = np.ascontiguousarray(u, dtype=np.float64)
     M, P = J.shape[0], len(inputs)
-    pb, keep = make_problem(N, K, dt, chi, M, C, P, cutoff, mask, g_fixed)
+    pb, keep = make_problem(N, K, dt, chi, M, C, P, cutoff, mask, g_fixed, crosstalk=crosstalk)
     ins, kin = _descs(inputs)
     tgs, ktg = _descs(targets)
     F = np.zeros(1)
@@ -168,6 +181,14 @@ def fidelity_static(N, K, dt, chi, C, inputs, targets, u, J, cutoff=1e-12, mask=
     _check(lib().tnrc_fidelity_static(ctypes.byref(pb), ins, tgs, _dp(u), _dp(J), ctypes.c_void_p(stream or 0),
                                       _dp(F), _dp(pt) if pt is not None else None), "tnrc_fidelity_static")
     return (F[0], pt.reshape(M, P)) if per_traj else F[0]
+
+
+def measure_fp64_peak(scratch_ptr: int, scratch_bytes: int) -> float:
+    """FP64 FMA throughput of the current device in GFLOP/s (see the header)."""
+    g = np.zeros(1)
+    _check(lib().tnrc_measure_fp64_peak(ctypes.c_void_p(scratch_ptr), scratch_bytes, _dp(g)),
+           "tnrc_measure_fp64_peak")
+    return float(g[0])
 
 
 def footprint(N, K, dt, chi, M, C, P, **kw) -> int:
@@ -180,14 +201,15 @@ class Context:
 
     def __init__(self, N: int, K: int, dt: float, chi: int, M: int, C: int, inputs: Sequence, targets: Sequence,
                  cutoff: float = 1e-12, mask=None, g_fixed=None, checkpoint_every: int = 0,
-                 stream: Optional[int] = None, warps: int = 0, ctas_per_sm: int = 0):
+                 stream: Optional[int] = None, warps: int = 0, ctas_per_sm: int = 0, crosstalk: int = 1):
         L = lib()
         self.N, self.K, self.C, self.M, self.P = N, K, C, M, len(inputs)
         self.stream = int(stream or 0)
+        self.terms = 3 if crosstalk == 3 else 1
         if len(targets) != self.P:
             raise ValueError("inputs and targets differ in length")
         pb, keep = make_problem(N, K, dt, chi, M, C, self.P, cutoff, mask, g_fixed, checkpoint_every, warps,
-                                ctas_per_sm)
+                                ctas_per_sm, crosstalk)
         packs = [_pack(s) for s in list(inputs) + list(targets)]
         descs = (MPSDesc * len(packs))()
         for d, (dims, data) in zip(descs, packs):
@@ -223,52 +245,56 @@ class Context:
     # -- inputs --
     def set_controls(self, u: np.ndarray):
         u = np.ascontiguousarray(u, dtype=np.float64)
-        _check(lib().tnrc_set_controls(self._h, _dp(u), u.size), "tnrc_set_controls")
+        _check(lib().tnrc_set_controls(self._h, _dp(u), u.size), "tnrc_set_controls", self._h)
 
     def set_controls_dev(self, ptr: int):
-        _check(lib().tnrc_set_controls_dev(self._h, ctypes.c_void_p(ptr)), "tnrc_set_controls_dev")
+        _check(lib().tnrc_set_controls_dev(self._h, ctypes.c_void_p(ptr)), "tnrc_set_controls_dev", self._h)
 
     def sample_noise(self, seed: int, dist: int, scale: float):
-        _check(lib().tnrc_sample_noise(self._h, ctypes.c_uint64(seed), dist, scale), "tnrc_sample_noise")
+        _check(lib().tnrc_sample_noise(self._h, ctypes.c_uint64(seed), dist, scale), "tnrc_sample_noise", self._h)
 
     def set_noise(self, J: np.ndarray):
         J = np.ascontiguousarray(J, dtype=np.float64)
-        _check(lib().tnrc_set_noise(self._h, _dp(J), J.size), "tnrc_set_noise")
+        _check(lib().tnrc_set_noise(self._h, _dp(J), J.size), "tnrc_set_noise", self._h)
 
     def get_noise(self) -> np.ndarray:
-        J = np.zeros((self.M, self.N - 1))
-        _check(lib().tnrc_get_noise(self._h, _dp(J), J.size), "tnrc_get_noise")
+        J = np.zeros((self.M, self.N - 1) if self.terms == 1 else (self.M, self.N - 1, 3))
+        _check(lib().tnrc_get_noise(self._h, _dp(J), J.size), "tnrc_get_noise", self._h)
         return J
 
     # -- evaluations --
     def fidelity(self, per_traj: bool = False):
         F = np.zeros(1)
         pt = np.zeros(self.M * self.P) if per_traj else None
-        _check(lib().tnrc_fidelity(self._h, _dp(F), _dp(pt) if pt is not None else None), "tnrc_fidelity")
+        _check(lib().tnrc_fidelity(self._h, _dp(F), _dp(pt) if pt is not None else None), "tnrc_fidelity", self._h)
         return (F[0], pt.reshape(self.M, self.P)) if per_traj else F[0]
 
     def fidelity_grad(self):
         F = np.zeros(1)
         g = np.zeros((self.K, self.C, self.N))
-        _check(lib().tnrc_fidelity_grad(self._h, _dp(F), _dp(g)), "tnrc_fidelity_grad")
+        _check(lib().tnrc_fidelity_grad(self._h, _dp(F), _dp(g)), "tnrc_fidelity_grad", self._h)
         return F[0], g
 
     def overlaps(self) -> np.ndarray:
         o = np.zeros(2 * self.M * self.P)
-        _check(lib().tnrc_get_overlaps(self._h, _dp(o), o.size), "tnrc_get_overlaps")
+        _check(lib().tnrc_get_overlaps(self._h, _dp(o), o.size), "tnrc_get_overlaps", self._h)
         return o.view(np.complex128).reshape(self.M, self.P)
 
     def evaluate_dev(self, F_ptr: int, grad_ptr: int = 0, per_traj_ptr: int = 0):
         _check(lib().tnrc_evaluate_dev(self._h, ctypes.c_void_p(F_ptr), ctypes.c_void_p(grad_ptr or None),
-                                       ctypes.c_void_p(per_traj_ptr or None)), "tnrc_evaluate_dev")
+                                       ctypes.c_void_p(per_traj_ptr or None)), "tnrc_evaluate_dev", self._h)
+
+    def set_graphs(self, enable: bool = True):
+        _check(lib().tnrc_set_graphs(self._h, 1 if enable else 0), "tnrc_set_graphs", self._h)
 
     def sync(self):
-        _check(lib().tnrc_sync(self._h), "tnrc_sync")
+        _check(lib().tnrc_sync(self._h), "tnrc_sync", self._h)
 
     def stats(self) -> dict:
         s = Stats()
-        _check(lib().tnrc_get_stats(self._h, ctypes.byref(s)), "tnrc_get_stats")
+        _check(lib().tnrc_get_stats(self._h, ctypes.byref(s)), "tnrc_get_stats", self._h)
         return {"updates": s.updates, "jacobi_sweeps": s.jacobi_sweeps, "max_bond": s.max_bond,
                 "bond_hist": [int(s.bond_hist[i]) for i in range(s.hist_len)],
                 "discarded_weight": s.discarded_weight, "last_ms": s.last_ms, "alg_flops": s.alg_flops,
-                "traj_ms": s.traj_ms, "traj_launches": s.traj_launches, "restarts": s.restarts}
+                "traj_ms": s.traj_ms, "traj_launches": s.traj_launches, "restarts": s.restarts,
+                "phase_cycles": dict(zip(PHASES, (int(x) for x in s.phase_cycles)))}

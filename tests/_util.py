@@ -19,14 +19,14 @@ def oracle_problem(w, u, mask, J, inputs, targets, g_fixed=None):
 def gpu_context(w, inputs, targets, mask, g_fixed=None, checkpoint_every=0):
     from paper_2603_03639_gb300 import Context
     return Context(w.N, w.K, w.dt, w.chi, w.M, w.C, inputs, targets, cutoff=w.sv_cutoff, mask=mask,
-                   g_fixed=g_fixed, checkpoint_every=checkpoint_every)
+                   g_fixed=g_fixed, checkpoint_every=checkpoint_every, crosstalk=w.crosstalk)
 
 
 def case(w, u=None):
     """(u, mask, J, inputs, targets) for workload w with oracle-drawn noise."""
     ins, tgs = w.states()
     u = w.controls() if u is None else u
-    J = noise.sample_J(w.seed_J, w.M, w.N, w.noise_dist, w.noise_scale)
+    J = noise.sample_J(w.seed_J, w.M, w.N, w.noise_dist, w.noise_scale, terms=w.crosstalk)
     return u, w.mask(), J, ins, tgs
 
 

@@ -42,10 +42,12 @@ def _worker(rank, world, port, out):
 
 
 @pytest.mark.parametrize("dist_kind", [0, 1])
-def test_shard_seeds_reproduce_the_global_noise(dist_kind):
+@pytest.mark.parametrize("terms", [1, 3])
+def test_shard_seeds_reproduce_the_global_noise(dist_kind, terms):
     N, M_local, R = 6, 3, 4
-    J_global = noise.sample_J(99, M_local * R, N, dist_kind, 0.1)
-    parts = [noise.sample_J(shard_seed(99, r, M_local, N, dist_kind), M_local, N, dist_kind, 0.1) for r in range(R)]
+    J_global = noise.sample_J(99, M_local * R, N, dist_kind, 0.1, terms=terms)
+    parts = [noise.sample_J(shard_seed(99, r, M_local, N, dist_kind, terms), M_local, N, dist_kind, 0.1, terms=terms)
+             for r in range(R)]
     assert np.array_equal(np.concatenate(parts), J_global)
 
 

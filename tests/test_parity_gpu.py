@@ -109,14 +109,24 @@ def test_checkpoint_segments_do_not_change_results(monkeypatch):
         assert F == res[0][0] and np.array_equal(g, res[0][1])
 
 
-def test_device_noise_matches_oracle_generator():
+def test_heisenberg_crosstalk_parity():
+    """The general parasitic model of Eq. Hp: J^x XX + J^y YY + J^z ZZ per bond."""
+    w = synth.WORKLOADS["cnot50"].replace(N=8, K=6, chi=16, M=3, P=2, crosstalk=3, noise_dist=0, noise_scale=0.2)
+    _, (F, g, O), (Fo, go, Oo) = run_both(w)
+    assert abs(F - Fo) <= TOL_F
+    assert np.max(np.abs(O - Oo)) <= TOL_O
+    assert grad_close(g, go)
+
+
+@pytest.mark.parametrize("terms", [1, 3])
+def test_device_noise_matches_oracle_generator(terms):
     for dist, scale in ((0, 0.1), (1, 0.05)):
-        w = synth.WORKLOADS["x8"].replace(M=37, noise_dist=dist, noise_scale=scale)
+        w = synth.WORKLOADS["x8"].replace(M=37, noise_dist=dist, noise_scale=scale, crosstalk=terms)
         u, mask, _, ins, tgs = case(w)
         ctx = gpu_context(w, ins, tgs, mask)
         ctx.sample_noise(w.seed_J, dist, scale)
         Jg = ctx.get_noise()
-        Jo = noise.sample_J(w.seed_J, w.M, w.N, dist, scale)
+        Jo = noise.sample_J(w.seed_J, w.M, w.N, dist, scale, terms=terms)
         if dist == 0:
             assert np.array_equal(Jg, Jo)
         else:
@@ -200,3 +210,45 @@ def test_packed_history_and_checkpoint_fallback_agree(monkeypatch):
         assert st["restarts"] == (w.M * w.P if cap == "0" else 0)
     assert out["0"][0] == out["none"][0]
     assert np.array_equal(out["0"][1], out["none"][1])
+
+
+def test_graph_replay_equals_plain_launches():
+    """tnrc_evaluate_dev through captured CUDA graphs (with and without the
+    gate rebuild) gives bitwise the plain launches' results."""
+    import torch
+    w = synth.WORKLOADS["x8"].replace(M=4, P=2)
+    u, mask, J, ins, tgs = case(w)
+    u2 = u + 0.01
+    side = torch.cuda.Stream()
+    stream = side.cuda_stream
+    outs = {}
+    from paper_2603_03639_gb300 import Context, TNRCError
+    legacy = Context(w.N, w.K, w.dt, w.chi, w.M, w.C, ins, tgs, mask=mask)
+    with pytest.raises(TNRCError):
+        legacy.set_graphs(True)          # the legacy default stream cannot be captured
+    legacy.close()
+    torch.cuda.synchronize()
+    for graphs in (False, True):
+        ctx = Context(w.N, w.K, w.dt, w.chi, w.M, w.C, ins, tgs, mask=mask, stream=stream)
+        ctx.set_graphs(graphs)
+        ctx.set_noise(J)
+        F = torch.zeros(1, dtype=torch.float64, device="cuda")
+        g = torch.zeros(u.shape, dtype=torch.float64, device="cuda")
+        res = []
+        torch.cuda.synchronize()
+        for uu in (u, u2, u2, u):
+            ud = torch.tensor(uu, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            ctx.set_controls_dev(ud.data_ptr())
+            ctx.evaluate_dev(F.data_ptr(), g.data_ptr())
+            ctx.sync()
+            res.append((F.item(), g.cpu().numpy().copy()))
+        # same controls again without a new set: gates are current
+        ctx.evaluate_dev(F.data_ptr(), g.data_ptr())
+        ctx.sync()
+        res.append((F.item(), g.cpu().numpy().copy()))
+        ctx.close()
+        outs[graphs] = res
+    for (Fa, ga), (Fb, gb) in zip(outs[False], outs[True]):
+        assert Fa == Fb and np.array_equal(ga, gb)
+    assert outs[True][3][0] == outs[True][0][0]
