@@ -210,7 +210,7 @@ size_t tnrc_footprint(const tnrc_problem* problem);
 void tnrc_destroy(tnrc_ctx* ctx);
 
 /* Measure the current device's FP64 FMA throughput (GFLOP/s): 8 independent
- * FMA chains per thread on 4 CTAs x 256 threads per SM, best of 2 timed
+ * FMA chains per thread on 4 CTAs x 256 threads per SM, best of 4 timed
  * launches after a warm-up, on the legacy default stream.  `scratch` is a
  * device buffer of at least 4 * SMs * 256 doubles (written, not read).  The
  * roofline denominator of the trajectory kernel, which is bound by FP64

@@ -125,7 +125,7 @@ bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, boo
   // leave after the per-warp arrays, within the 227 KB a CTA may use
   {
     const int per_sm = 220 * 1024 / ctas_per_sm;
-    const int small = P.warps * (tnrc::kMaxDim * 12 + 64 * 16) + 1024;
+    const int small = (int)tnrc_traj_smem(P.warps, 0) + 1024;
     const int per_warp = std::max(0, per_sm - small) / P.warps / 16;
     P.slab_elems = std::max(256, std::min(4 * chi * chi, per_warp / 32 * 32));
   }

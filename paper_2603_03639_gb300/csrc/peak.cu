@@ -29,7 +29,7 @@ extern "C" tnrc_status tnrc_measure_fp64_peak(void* scratch, size_t scratch_byte
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return TNRC_E_CUDA;
-  const int threads = 256, blocks = 4 * n_sm, iters = 4096;
+  const int threads = 256, blocks = 4 * n_sm, iters = 16384;   // ~30 ms per launch
   if (scratch_bytes < (size_t)blocks * threads * sizeof(double)) return TNRC_E_INVALID;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return TNRC_E_CUDA;
@@ -39,7 +39,7 @@ extern "C" tnrc_status tnrc_measure_fp64_peak(void* scratch, size_t scratch_byte
   }
   double best = 0.0;
   bool ok = true;
-  for (int rep = 0; rep < 3 && ok; ++rep) {
+  for (int rep = 0; rep < 5 && ok; ++rep) {   // best of four after a warm-up launch
     ok = cudaEventRecord(e0, 0) == cudaSuccess;
     fp64_fma_chains<<<blocks, threads>>>(static_cast<double*>(scratch), iters, 0.999999, 1e-7);
     ok = ok && cudaGetLastError() == cudaSuccess && cudaEventRecord(e1, 0) == cudaSuccess &&

@@ -110,6 +110,121 @@ __device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, int lan
   return -kMaxSweeps;
 }
 
+// Householder QR with column pivoting, W P = Q R, of the m x n matrix W held
+// row-major (row i at W + i*n), by one warp; Q is not formed.  This is the
+// preconditioner of Drmac and Veselic ("New fast and accurate Jacobi SVD
+// algorithm", SIAM J. Matrix Anal. Appl. 29, 2008): one-sided Jacobi applied
+// to the columns of R^dagger converges in fewer sweeps than on the original
+// matrix, and R^dagger has only r columns where r is the numerical rank.
+//
+// Step j takes the remaining column of largest norm as pivot; when that norm
+// squared is <= thr, every remaining column is below it and the
+// factorisation stops with r = j.  Columns are shared out to groups of G lanes
+// (G * n <= 32 when n <= 32), each group's lanes splitting the rows; the
+// trailing column norms are recomputed exactly while the reflector is applied,
+// so the pivot choice needs no norm downdating.  Reductions within a group use
+// xor shuffles, so every lane of a group holds the same sums, and the pivot
+// reduction (integer comparisons of the non-negative norms' bit patterns, ties
+// to the smaller index) gives every lane the same pivot.
+//
+// On return rows 0..r-1 of W hold R (zeros below the diagonal; row j is the
+// j-th row of R in the pivoted column order), piv[c] is the original index of
+// pivoted column c (c < n), and qn (n doubles) has been used as scratch.
+__device__ inline int warp_qrcp(double2* W, int m, int n, double thr, int* piv, double* qn, int lane) {
+  int G = 1;
+  while (G < 32 && G * 2 * n <= 32) G <<= 1;
+  const int groups = 32 / G;
+  const int gi = lane / G, lig = lane & (G - 1);
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  for (int c = gi; c < n; c += groups) {
+    double q = 0.0;
+    for (int i = lig; i < m; i += G) q += cabs2(W[(size_t)i * n + c]);
+    for (int o = G >> 1; o > 0; o >>= 1) q += __shfl_xor_sync(gmask, q, o);
+    if (lig == 0) {
+      qn[c] = q;
+      piv[c] = c;
+    }
+  }
+  __syncwarp();
+  const int steps = m < n ? m : n;
+  for (int j = 0; j < steps; ++j) {
+    // pivot: the column c >= j of largest remaining norm
+    long long best = -1;
+    int bi = n;
+    for (int c = j + lane; c < n; c += 32) {
+      const long long v = __double_as_longlong(qn[c]);
+      if (v > best) {
+        best = v;
+        bi = c;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    const double xn2 = __longlong_as_double(best);
+    if (!(xn2 > thr)) return j;
+    if (bi != j) {
+      for (int i = lane; i < m; i += 32) {
+        const double2 t = W[(size_t)i * n + j];
+        W[(size_t)i * n + j] = W[(size_t)i * n + bi];
+        W[(size_t)i * n + bi] = t;
+      }
+      if (lane == 0) {
+        const int tp = piv[j];
+        piv[j] = piv[bi];
+        piv[bi] = tp;
+        qn[bi] = qn[j];
+        qn[j] = xn2;
+      }
+      __syncwarp();
+    }
+    // reflector H = I - beta v v^dag mapping column j (rows j..m-1) to alpha e_j:
+    // alpha = -e^{i arg x0} |x|, v = x - alpha e_j, beta = 1 / (|x| (|x| + |x0|))
+    const double2 x0 = W[(size_t)j * n + j];
+    const double xn = sqrt(xn2);
+    const double ax0 = sqrt(cabs2(x0));
+    const double2 ph = (ax0 > 0.0) ? cscale(x0, 1.0 / ax0) : make_double2(1.0, 0.0);
+    const double2 v0 = cscale(ph, ax0 + xn);
+    const double beta = 1.0 / (xn * (xn + ax0));
+    for (int c = gi; c < n; c += groups) {
+      if (c <= j) continue;
+      double2 s = make_double2(0.0, 0.0);
+      for (int i = j + lig; i < m; i += G) {
+        const double2 vi = (i == j) ? v0 : W[(size_t)i * n + j];
+        cfmac(s, vi, W[(size_t)i * n + c]);
+      }
+      for (int o = G >> 1; o > 0; o >>= 1) {
+        s.x += __shfl_xor_sync(gmask, s.x, o);
+        s.y += __shfl_xor_sync(gmask, s.y, o);
+      }
+      s = cscale(s, beta);
+      double q = 0.0;
+      for (int i = j + lig; i < m; i += G) {
+        const double2 vi = (i == j) ? v0 : W[(size_t)i * n + j];
+        double2 x = W[(size_t)i * n + c];
+        x.x = fma(-vi.x, s.x, x.x);
+        x.x = fma(vi.y, s.y, x.x);
+        x.y = fma(-vi.x, s.y, x.y);
+        x.y = fma(-vi.y, s.x, x.y);
+        W[(size_t)i * n + c] = x;
+        if (i > j) q += cabs2(x);
+      }
+      for (int o = G >> 1; o > 0; o >>= 1) q += __shfl_xor_sync(gmask, q, o);
+      if (lig == 0) qn[c] = q;
+    }
+    __syncwarp();
+    for (int i = j + lane; i < m; i += 32)
+      W[(size_t)i * n + j] = (i == j) ? make_double2(-xn * ph.x, -xn * ph.y) : make_double2(0.0, 0.0);
+    __syncwarp();
+  }
+  return steps;
+}
+
 // Column norms, ranking and the truncation decision after warp_jacobi.
 // sig2[j] = |column j|^2 (j < m); perm[i] = column of rank i (i < k), ranks by
 // decreasing sigma with ties broken by the smaller index.  Returns k =

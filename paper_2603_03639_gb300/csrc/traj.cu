@@ -28,7 +28,9 @@ struct WarpCtx {
   double2* slab;       // shared, slab_elems
   double2* scratch;    // global, scratch_elems
   double* sig2;        // shared, kMaxDim
+  double* qn;          // shared, kMaxDim (column norms of the pivoted QR)
   int* perm;           // shared, kMaxDim
+  int* piv;            // shared, kMaxDim (column pivots of the QR)
   double2* small;      // shared, 64 complex (four 4x4 matrices)
   int lane;
   long long sweeps;
@@ -80,6 +82,9 @@ __device__ __forceinline__ const double2* layer_gate(const TrajParams& p, int s,
 // ---------------------------------------------------------------------------
 // Two-site update of bond b: theta = lam_{b-1} G (B_b B_{b+1}), truncated SVD,
 // B_{b+1} <- Y_k^dag, B_b <- Phi Y_k / |S_k|, lam_b <- S_k / |S_k|.
+// The SVD: theta P = Q R by pivoted QR (Q not formed; R has r rows, r the
+// numerical rank), then one-sided Jacobi on the r columns of R^dagger:
+// R^dagger V = Z S, so theta = (Q V) S (P Z)^dagger and Y = P Z.
 // ---------------------------------------------------------------------------
 __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char* slot, int b, const double2* G,
                                 bool adjoint, bool record, bool count, WarpCtx& w) {
@@ -102,7 +107,7 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
 #pragma unroll
     for (int c = 0; c < 4; ++c) g[r * 4 + c] = adjoint ? cconj(G[c * 4 + r]) : G[r * 4 + c];
 
-  // Phase 1: Phi = G (B_b B_{b+1}) and theta^dagger (column (al s1), row (s2 ga)).
+  // Phase 1: Phi = G (B_b B_{b+1}) and theta, both row-major: row (al s1), column (s2 ga).
   TNRC_TIC(t_c);
   double fro = 0.0;
   for (int it = lane; it < Dl * Dr; it += 32) {
@@ -132,7 +137,7 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
         const size_t idx = (size_t)(al * 2 + s1) * n + s2 * Dr + ga;
         Phi[idx] = v;
         const double2 th = cscale(v, ll);
-        T[idx] = cconj(th);
+        T[idx] = th;
         fro += cabs2(th);
       }
   }
@@ -140,15 +145,21 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   __syncwarp();
   TNRC_TOC(w, 0, t_c);
 
-  // Phase 2: one-sided Jacobi on the m columns of theta^dagger.
+  // Phase 2: pivoted QR of theta, then one-sided Jacobi on the r columns of
+  // R^dagger (column j = conjugated row j of R, contiguous at T + j n).
   TNRC_TIC(t_j);
-  const int sw = warp_jacobi(T, n, m, fro, lane);
+  const double zthr = kJacobiZero * kJacobiZero * fro;
+  int r = warp_qrcp(T, m, n, zthr, w.piv, w.qn, lane);
+  if (r < 1) r = 1;  // theta == 0 (or not finite): keep one column; the NaN check below reports it
+  for (int e = lane; e < r * n; e += 32) T[e] = cconj(T[e]);
+  __syncwarp();
+  const int sw = warp_jacobi(T, n, r, fro, lane);
   TNRC_TOC(w, 1, t_j);
 
   // Phase 3: rank, truncate.
   TNRC_TIC(t_r);
   double kept2, tot2;
-  int k = warp_rank_truncate(T, n, m, chi, p.eps, w.sig2, w.perm, lane, kept2, tot2);
+  int k = warp_rank_truncate(T, n, r, chi, p.eps, w.sig2, w.perm, lane, kept2, tot2);
   if (k > Y.dcap[b + 1]) {  // cannot happen (k <= min(m, n, chi)); keeps memory in bounds regardless
     k = Y.dcap[b + 1];
     if (lane == 0) atomicOr(p.status, kStatusBadDims);
@@ -168,22 +179,24 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   const double inv_kn = rsqrt(kept2);
   TNRC_TOC(w, 2, t_r);
 
-  // Phase 4: write lam_b, B_{b+1} = Y_k^dag, B_b = Phi Y_k / |S_k|.
+  // Phase 4: write lam_b, B_{b+1} = Y_k^dag, B_b = Phi Y_k / |S_k|, where
+  // Y[piv[c]][i] = Z[c][i] = T[perm[i] n + c] / sigma_i.
   TNRC_TIC(t_w);
   double* lamw = lam + (size_t)b * lstride;
+  const int* piv = w.piv;
   for (int i = lane; i < k; i += 32) lamw[i] = sqrt(w.sig2[w.perm[i]]) * inv_kn;
   for (int it = lane; it < k * n; it += 32) {
-    const int i = it / n, r = it - i * n;
+    const int i = it / n, c = it - i * n;
     const int j = w.perm[i];
-    Bt[it] = cscale(cconj(T[(size_t)j * n + r]), rsqrt(w.sig2[j]));
+    Bt[(size_t)i * n + piv[c]] = cscale(cconj(T[(size_t)j * n + c]), rsqrt(w.sig2[j]));
   }
   for (int it = lane; it < m * k; it += 32) {
     const int row = it / k, i = it - row * k;
     const int j = w.perm[i];
     const double2* ph = Phi + (size_t)row * n;
-    const double2* y = T + (size_t)j * n;
+    const double2* z = T + (size_t)j * n;
     double2 acc = make_double2(0.0, 0.0);
-    for (int r = 0; r < n; ++r) cfma(acc, ph[r], y[r]);
+    for (int c = 0; c < n; ++c) cfma(acc, ph[piv[c]], z[c]);
     A[it] = cscale(acc, rsqrt(w.sig2[j]) * inv_kn);
   }
   __syncwarp();
@@ -730,14 +743,18 @@ __global__ void __launch_bounds__(kWarps * 32, 1) traj_kernel(TrajParams p) {
   const int lane = threadIdx.x & 31;
   double2* slabs = reinterpret_cast<double2*>(smem_raw);
   double* sig = reinterpret_cast<double*>(slabs + (size_t)p.warps * p.slab_elems);
-  int* perms = reinterpret_cast<int*>(sig + (size_t)p.warps * kMaxDim);
-  double2* smalls = reinterpret_cast<double2*>(perms + (size_t)p.warps * kMaxDim);
+  double* qns = sig + (size_t)p.warps * kMaxDim;
+  int* perms = reinterpret_cast<int*>(qns + (size_t)p.warps * kMaxDim);
+  int* pivs = perms + (size_t)p.warps * kMaxDim;
+  double2* smalls = reinterpret_cast<double2*>(pivs + (size_t)p.warps * kMaxDim);
 
   WarpCtx w;
   w.slab = slabs + (size_t)warp * p.slab_elems;
   w.scratch = p.warp_scratch + ((size_t)blockIdx.x * p.warps + warp) * p.scratch_elems;
   w.sig2 = sig + (size_t)warp * kMaxDim;
   w.perm = perms + (size_t)warp * kMaxDim;
+  w.qn = qns + (size_t)warp * kMaxDim;
+  w.piv = pivs + (size_t)warp * kMaxDim;
   w.small = smalls + (size_t)warp * 64;
   w.lane = lane;
   w.sweeps = 0;
@@ -801,6 +818,6 @@ extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, siz
 }
 
 extern "C" size_t tnrc_traj_smem(int warps, int slab_elems) {
-  return (size_t)warps * slab_elems * sizeof(double2) + (size_t)warps * tnrc::kMaxDim * (sizeof(double) + sizeof(int)) +
+  return (size_t)warps * slab_elems * sizeof(double2) + (size_t)warps * tnrc::kMaxDim * 2 * (sizeof(double) + sizeof(int)) +
          (size_t)warps * 64 * sizeof(double2);
 }
