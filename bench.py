@@ -170,6 +170,34 @@ def reference_arm(args, w):
 # GPU leg
 # --------------------------------------------------------------------------
 
+KERNEL_SOURCES = ("svd_warp.cuh", "tnrc_device.cuh", "traj.cu")
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per trajectory-kernel launch from the committed ncu summary
+    for this workload, or None when there is none or the kernel sources have
+    changed since it was taken (the summary records their SHA-256)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traj_kernel_%s_traffic.txt" % workload)
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        key, sep, val = line.partition(":")
+        if sep and key.strip() and " " not in key.strip():
+            rec[key.strip()] = val.strip()
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2603_03639_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    if rec.get("workload") != workload or rec.get("kernel_sources_sha256") != h.hexdigest():
+        return None
+    try:
+        return int(rec["bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def gpu_arm(args, w):
     import torch
     import torch.distributed as dist
@@ -274,15 +302,7 @@ def gpu_arm(args, w):
     torch.cuda.synchronize(dev)
     measured_peak = measure_fp64_peak(probe.data_ptr(), probe.numel() * 8) / 1e3
     achieved = (alg / launches) / (traj_ms / launches / 1000.0) / 1e12 if launches else None
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traj_kernel_traffic.json")
-    if os.path.exists(prof):
-        try:
-            pj = json.load(open(prof))
-            if pj.get("workload") == w.name and pj.get("bytes_per_launch"):
-                traffic = pj["bytes_per_launch"]
-        except Exception:
-            traffic = None
+    traffic = recorded_traffic(w.name)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -296,6 +316,9 @@ def gpu_arm(args, w):
                          "source": "autotune cache" if tuned[0] else "default"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "traffic_source": ("ncu dram bytes of a 152-trajectory launch scaled to this launch's "
+                                        "trajectories (profiles/traj_kernel_%s_traffic.txt)" % w.name)
+                     if traffic else "no ncu record for these kernel sources",
                      "kernel": "tnrc::traj_kernel",
                      "peak_source": "derived FP64 FMA peak: 2 DFMA/clk/SM x 152 SMs x 2070 MHz",
                      "measured_fp64_fma_peak": measured_peak,
