@@ -15,6 +15,7 @@ namespace tnrc {
 
 __global__ void canon_kernel(CanonArgs a) {
   __shared__ double sig2[256];
+  __shared__ double cn[256];
   __shared__ int perm[256];
   __shared__ int D[257];
   const int lane = threadIdx.x;
@@ -55,7 +56,7 @@ __global__ void canon_kernel(CanonArgs a) {
     }
     fro = warp_sum(fro);
     __syncwarp();
-    const int sw = warp_jacobi(T, n, m, fro, lane);
+    const int sw = warp_jacobi(T, n, m, fro, cn, lane);
     int r = warp_rank_truncate(T, n, m, m, a.eps, sig2, perm, lane, kept2, tot2);
     if (r > n) r = n;
     if (lane == 0 && sw < 0) atomicOr(a.status, kStatusNoConverge);
@@ -121,7 +122,7 @@ __global__ void canon_kernel(CanonArgs a) {
     }
     fro = warp_sum(fro);
     __syncwarp();
-    const int sw = warp_jacobi(T, n, m, fro, lane);
+    const int sw = warp_jacobi(T, n, m, fro, cn, lane);
     int k = warp_rank_truncate(T, n, m, a.chi, a.eps, sig2, perm, lane, kept2, tot2);
     if (k > n) k = n;
     if (lane == 0 && sw < 0) atomicOr(a.status, kStatusNoConverge);

@@ -28,8 +28,16 @@ __device__ __forceinline__ void rr_pair(int mp, int r, int q, int& i, int& j) {
 }
 
 // Returns the number of sweeps (the last one made no rotation), or -kMaxSweeps
-// when the sweep limit was reached.  fro2 = squared Frobenius norm of T.
-__device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, int lane) {
+// when the sweep limit was reached.  fro2 = squared Frobenius norm of T;
+// cn: shared scratch of m doubles holding the column norms squared.
+//
+// The norms are computed exactly before the first sweep and in the first
+// round of every sweep (where the pair's lanes form all three inner
+// products); in the other rounds only <a, b> is formed and the norms are
+// carried through each rotation by |a'|^2 = |a|^2 - t |<a,b>|,
+// |b'|^2 = |b|^2 + t |<a,b>| (t = tan theta), recomputed from the rotated
+// column should a norm fall below 1/16 of its old value (cancellation).
+__device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, double* cn, int lane) {
   const int mp = m + (m & 1);
   if (mp < 2 || n < 1) return 0;
   const int P = mp >> 1;
@@ -41,6 +49,13 @@ __device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, int lan
   const double thr = kJacobiZero * kJacobiZero * fro2;
   const double tol = 2.0 * (double)(m > n ? m : n) * 2.220446049250313e-16;
   const double tol2 = tol * tol;
+  for (int c = lane; c < m; c += 32) {
+    const double2* col = T + (size_t)c * n;
+    double s = 0.0;
+    for (int row = 0; row < n; ++row) s = fma(col[row].x, col[row].x, fma(col[row].y, col[row].y, s));
+    cn[c] = s;
+  }
+  __syncwarp();
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
     int rotated = 0;
     for (int r = 0; r < mp - 1; ++r) {
@@ -50,57 +65,80 @@ __device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, int lan
         if (i >= m || j >= m) continue;  // the padding column of an odd m is zero
         double2* a = T + (size_t)i * n;
         double2* b = T + (size_t)j * n;
-        double aa = 0.0, bb = 0.0;
+        double aa, bb;
         double2 ab = make_double2(0.0, 0.0);
-        for (int row = lig; row < n; row += g) {
-          const double2 x = a[row], y = b[row];
-          aa = fma(x.x, x.x, fma(x.y, x.y, aa));
-          bb = fma(y.x, y.x, fma(y.y, y.y, bb));
-          cfmac(ab, x, y);
+        if (r == 0) {
+          aa = 0.0;
+          bb = 0.0;
+          for (int row = lig; row < n; row += g) {
+            const double2 x = a[row], y = b[row];
+            aa = fma(x.x, x.x, fma(x.y, x.y, aa));
+            bb = fma(y.x, y.x, fma(y.y, y.y, bb));
+            cfmac(ab, x, y);
+          }
+          for (int o = g >> 1; o > 0; o >>= 1) {
+            aa += __shfl_xor_sync(gmask, aa, o);
+            bb += __shfl_xor_sync(gmask, bb, o);
+            ab.x += __shfl_xor_sync(gmask, ab.x, o);
+            ab.y += __shfl_xor_sync(gmask, ab.y, o);
+          }
+        } else {
+          aa = cn[i];
+          bb = cn[j];
+          for (int row = lig; row < n; row += g) cfmac(ab, a[row], b[row]);
+          for (int o = g >> 1; o > 0; o >>= 1) {
+            ab.x += __shfl_xor_sync(gmask, ab.x, o);
+            ab.y += __shfl_xor_sync(gmask, ab.y, o);
+          }
         }
-        for (int o = g >> 1; o > 0; o >>= 1) {
-          aa += __shfl_xor_sync(gmask, aa, o);
-          bb += __shfl_xor_sync(gmask, bb, o);
-          ab.x += __shfl_xor_sync(gmask, ab.x, o);
-          ab.y += __shfl_xor_sync(gmask, ab.y, o);
-        }
+        double na = aa, nb = bb;
         const double ab2 = cabs2(ab);
         if (aa > thr && bb > thr && ab2 > tol2 * aa * bb) {
           rotated = 1;
-          // Real rotation of the pair after the phase of <a,b> is divided out:
-          // zeta = (|b|^2 - |a|^2) / (2|<a,b>|) = cot(2 theta).  With
-          // r = 1/sqrt(1 + zeta^2) = |sin 2theta| and q = |zeta| r = cos 2theta,
-          // c = sqrt((1 + q)/2) and s = sign(zeta) r / (2c): two reciprocal
-          // square roots, no cancellation, c^2 + s^2 = 1 to rounding.
-          const double inv = rsqrt(ab2);
-          const double zeta = (bb - aa) * 0.5 * inv;
-          const double az = fabs(zeta);
-          double r, q;
-          if (az > 1e150) {
-            r = 1.0 / az;
-            q = 1.0;
-          } else {
-            r = rsqrt(fma(zeta, zeta, 1.0));
-            q = az * r;
-          }
-          const double hq = 0.5 * (1.0 + q);
+          // Real rotation of the pair after the phase of <a,b> is divided out,
+          // cot(2 theta) = (|b|^2 - |a|^2) / (2 |<a,b>|).  With d = |b|^2 - |a|^2
+          // and w = 1 / sqrt(d^2 + 4 |<a,b>|^2): cos 2theta = |d| w,
+          // sin 2theta = 2 |<a,b>| w, c = sqrt((1 + cos 2theta) / 2) and
+          // s e^{i phi} = sign(d) w / sqrt((1 + cos 2theta) / 2) <a,b> -- two
+          // reciprocal square roots, no division, no cancellation.
+          const double d = bb - aa;
+          const double w = rsqrt(fma(d, d, 4.0 * ab2));
+          const double hq = fma(0.5, fabs(d) * w, 0.5);   // c^2
           const double rc = rsqrt(hq);
           const double c = hq * rc;
-          const double s = copysign(0.5 * r * rc, zeta);
-          const double2 sp = make_double2(s * ab.x * inv, s * ab.y * inv);  // s e^{i phi}
+          const double f = copysign(w * rc, d);
+          const double2 sp = make_double2(f * ab.x, f * ab.y);  // s e^{i phi}
           // a <- c a - conj(sp) b ;  b <- c b + sp a
           for (int row = lig; row < n; row += g) {
             const double2 x = a[row], y = b[row];
-            double2 na = cscale(x, c);
-            na.x = fma(-sp.x, y.x, na.x);
-            na.x = fma(-sp.y, y.y, na.x);
-            na.y = fma(-sp.x, y.y, na.y);
-            na.y = fma(sp.y, y.x, na.y);
-            double2 nb = cscale(y, c);
-            cfma(nb, sp, x);
-            a[row] = na;
-            b[row] = nb;
+            double2 na_ = cscale(x, c);
+            na_.x = fma(-sp.x, y.x, na_.x);
+            na_.x = fma(-sp.y, y.y, na_.x);
+            na_.y = fma(-sp.x, y.y, na_.y);
+            na_.y = fma(sp.y, y.x, na_.y);
+            double2 nb_ = cscale(y, c);
+            cfma(nb_, sp, x);
+            a[row] = na_;
+            b[row] = nb_;
           }
+          // t |<a,b>| = sign(d) 2 |<a,b>|^2 w; c^2 = hq, s^2 = 1 - hq
+          const double dl = copysign(2.0 * ab2 * w, d);
+          na = fma(hq, aa, fma(1.0 - hq, bb, -dl));
+          nb = fma(hq, bb, fma(1.0 - hq, aa, dl));
+          if (na < 0.0625 * aa) {
+            na = 0.0;
+            for (int row = lig; row < n; row += g) na = fma(a[row].x, a[row].x, fma(a[row].y, a[row].y, na));
+            for (int o = g >> 1; o > 0; o >>= 1) na += __shfl_xor_sync(gmask, na, o);
+          }
+          if (nb < 0.0625 * bb) {
+            nb = 0.0;
+            for (int row = lig; row < n; row += g) nb = fma(b[row].x, b[row].x, fma(b[row].y, b[row].y, nb));
+            for (int o = g >> 1; o > 0; o >>= 1) nb += __shfl_xor_sync(gmask, nb, o);
+          }
+        }
+        if (lig == 0) {
+          cn[i] = na;
+          cn[j] = nb;
         }
       }
       __syncwarp();

@@ -153,7 +153,7 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   if (r < 1) r = 1;  // theta == 0 (or not finite): keep one column; the NaN check below reports it
   for (int e = lane; e < r * n; e += 32) T[e] = cconj(T[e]);
   __syncwarp();
-  const int sw = warp_jacobi(T, n, r, fro, lane);
+  const int sw = warp_jacobi(T, n, r, fro, w.qn, lane);   // qn is free after the QR
   TNRC_TOC(w, 1, t_j);
 
   // Phase 3: rank, truncate.
