@@ -28,12 +28,65 @@ def mps_vector(sites):
     return v / np.linalg.norm(v)
 
 
-def trajectory(pb: "_r.Problem", s, p, want_grad=True):
-    """(O, dO) for one trajectory with dense vectors and the costate formula."""
+def apply_one_site(psi, U, j, N):
+    v = psi.reshape(2 ** j, 2, 2 ** (N - j - 1))
+    return np.einsum("ij,ajc->aic", U, v).reshape(-1)
+
+
+def first_order_trajectory(pb: "_r.Problem", s, p, want_grad=True):
+    """(O, dO) with the slice of Eq. circuit applied literally to a dense
+    vector: per Trotter step (dt / substeps) of bin k, exp(-i dts V_b) on
+    every bond (odd bonds, then even bonds; V_b = c ZZ + J^x XX + J^y YY),
+    then exp(-i dts y_j Y) on every site, then exp(-i dts x_j X) on every
+    site.  The gradient is the costate formula of App. A with its factor
+    -i dts and each derivative taken at its own factor:
+    dO/du = <b| (-i dts P) |a> right after the factor u enters, P = ZZ, X_j or Y_j."""
     N = pb.N
     a = mps_vector(pb.inputs[p])
     t = mps_vector(pb.targets[p])
-    sched = _r.layers(pb.K, pb.dt)
+    dts = pb.dt / pb.substeps
+    ops = []   # (kind, where, U, (k, c, i) or None, generator) in time order
+    for k in range(pb.K):
+        for _ in range(pb.substeps):
+            for b in list(range(1, N - 1, 2)) + list(range(0, N - 1, 2)):
+                xl, yl, xr, yr, c, jx, jy = _r.bond_params(pb, s, k, b)
+                h = c * np.kron(_g.Z, _g.Z) + jx * np.kron(_g.X, _g.X) + jy * np.kron(_g.Y, _g.Y)
+                G = _g.expm_hermitian(h, dts)[0]
+                slot = (k, 2, b) if (pb.C == 3 and pb.mask[2, b]) else None
+                ops.append((2, b, G, slot, np.kron(_g.Z, _g.Z)))
+            for cidx, P in ((1, _g.Y), (0, _g.X)):
+                for j in range(N):
+                    amp = pb.u[k, cidx, j] * pb.mask[cidx, j]
+                    U = np.cos(dts * amp) * _g.I2 - 1j * np.sin(dts * amp) * P
+                    ops.append((1, j, U, (k, cidx, j) if pb.mask[cidx, j] else None, P))
+    hist = [a]
+    for (kind, wh, U, _, _) in ops:
+        a = apply_two_site(a, U, wh, N) if kind == 2 else apply_one_site(a, U, wh, N)
+        hist.append(a)
+    O = np.vdot(t, a)
+    if not want_grad:
+        return O, None
+    dO = np.zeros((pb.K, pb.C, N), dtype=np.complex128)
+    c = t.copy()
+    for i in range(len(ops) - 1, -1, -1):
+        kind, wh, U, slot, P = ops[i]
+        if slot is not None:
+            Q = -1j * dts * P
+            v = apply_two_site(hist[i + 1], Q, wh, N) if kind == 2 else apply_one_site(hist[i + 1], Q, wh, N)
+            dO[slot] += np.vdot(c, v)
+        Ud = U.conj().T
+        c = apply_two_site(c, Ud, wh, N) if kind == 2 else apply_one_site(c, Ud, wh, N)
+    return O, dO
+
+
+def trajectory(pb: "_r.Problem", s, p, want_grad=True):
+    """(O, dO) for one trajectory with dense vectors and the costate formula."""
+    if pb.order == 1:
+        return first_order_trajectory(pb, s, p, want_grad)
+    N = pb.N
+    a = mps_vector(pb.inputs[p])
+    t = mps_vector(pb.targets[p])
+    sched = _r.layers(pb.K, pb.dt, pb.substeps)
     hist = [a]
     gl_all = []
     for (k, par, tau) in sched:

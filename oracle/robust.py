@@ -1,25 +1,38 @@
 """Ensemble-averaged fidelity and its costate gradient (Sec. II state form;
 App. A), one trajectory (noise sample s, input p) at a time.
 
-Time discretisation.  Slice k (k = 0..K-1) of length dt is the second-order
-split A(dt/2) B(dt) A(dt/2): layer A applies exp(-i tau h_b) on every even
-bond b, layer B on every odd bond, with h_b the bond Hamiltonian of
-``oracle.gates`` built from slice k's controls.  One slice = one control bin.
-The MPS is compressed after every time step (Sec. II): the half layer A(dt/2)
-that ends slice k and the one that starts slice k+1 act on the same bonds with
+Time discretisation.  Control bin k (k = 0..K-1) of length dt holds the
+controls u[k]; it is split into n_sub equal Trotter steps of length
+dts = dt / n_sub (one step per bin unless stated otherwise).
+
+Second order (the default): each step is A(dts/2) B(dts) A(dts/2): layer A
+applies exp(-i tau h_b) on every even bond b, layer B on every odd bond, with
+h_b the bond Hamiltonian of ``oracle.gates`` built from the bin's controls.
+The MPS is compressed after every time step (Sec. II): the half layer A that
+ends one step and the one that starts the next act on the same bonds with
 nothing in between, so they are applied as one gate (their product) followed
-by one truncated SVD.  The truncated layers are therefore
-    A_0, B_0, A_0 A_1, B_1, A_1 A_2, ..., B_{K-1}, A_{K-1}   (2K + 1 layers).
+by one truncated SVD.  With S = K n_sub steps the truncated layers are
+    A_0, B_0, A_0 A_1, B_1, A_1 A_2, ..., B_{S-1}, A_{S-1}   (2S + 1 layers).
+
+First order (Eq. circuit): each step applies, right to left,
+exp(-i dts V_b) on every bond (V_b = c_b ZZ + J^x XX + J^y YY, odd bonds
+first, then even bonds), then exp(-i dts y_j Y_j) on every site, then
+exp(-i dts x_j X_j) on every site.  Single-site gates do not change the
+Schmidt values, so each site's two rotations are folded into the one bond
+gate of the step that touches it last: the even bond (j or j-1) for every
+site of an even chain, and for an odd chain the last site goes with the odd
+bond N-2.  Truncated layers: (odd V), (even V with folded rotations), per
+step (2S layers).
 
 Objective.  O_sp = <t_p | a_sp(T)>, F = (1/(M P)) sum_sp |O_sp|^2, the
 fidelity whose complement is the ensemble-averaged state infidelity of Sec. II.
 
-Gradient.  With layers l = 1..L (L = 3K), a_l the truncated state after layer
+Gradient.  With truncated layers l = 1..L, a_l the truncated state after layer
 l and b_l = L_{l+1}^dag ... L_L^dag t (the costate, truncated by the same rule),
 O = <b_l | L_l | a_{l-1}> for every l (App. A), so for a parameter u inside the
-gate G of bond b in layer l:
-    dO/du += <b_l | (dG/du) G^dagger | a_l>,
-summed over every gate the parameter enters.  dF/du = (2/(MP)) sum Re(conj(O) dO/du).
+factor G_f of the gate of bond b in layer l (gate = G_n ... G_1):
+    dO/du += <b_l | L_f (dG_f/du) G_f^dagger L_f^dagger | a_l>,  L_f = G_n ... G_{f+1},
+summed over every factor the parameter enters.  dF/du = (2/(MP)) sum Re(conj(O) dO/du).
 Without truncation this is the exact derivative of the discrete map.
 """
 import dataclasses
@@ -45,6 +58,8 @@ class Problem:
     targets: list
     g_fixed: Optional[np.ndarray] = None   # [K][N-1]
     eps: float = 1e-12
+    order: int = 2                # Trotter order: 2 (A B A) or 1 (Eq. circuit)
+    substeps: int = 1             # Trotter steps per control bin
 
     @property
     def M(self):
@@ -55,23 +70,61 @@ class Problem:
         return len(self.inputs)
 
 
-def layers(K, dt):
-    """[(k, parity, tau)] of the elementary gate layers in time order."""
+def layers(K, dt, substeps=1):
+    """[(k, parity, tau)] of the elementary gate layers of the second-order
+    split in time order (bin k, Trotter step of length dt / substeps)."""
     out = []
+    dts = dt / substeps
     for k in range(K):
-        out += [(k, 0, dt / 2.0), (k, 1, dt), (k, 0, dt / 2.0)]
+        for _ in range(substeps):
+            out += [(k, 0, dts / 2.0), (k, 1, dts), (k, 0, dts / 2.0)]
     return out
 
 
-def merged_layers(K, dt):
-    """[(parity, [(k, tau), ...])]: the truncated layers, each the product of
-    the listed elementary layers (first in time first)."""
-    out = [(0, [(0, dt / 2.0)])]
-    for k in range(K):
-        out.append((1, [(k, dt)]))
-        if k + 1 < K:
-            out.append((0, [(k, dt / 2.0), (k + 1, dt / 2.0)]))
-    out.append((0, [(K - 1, dt / 2.0)]))
+def merged_layers(K, dt, substeps=1):
+    """[(parity, [(k, tau), ...])]: the truncated layers of the second-order
+    split, each the product of the listed elementary layers (first in time
+    first)."""
+    S = K * substeps
+    dts = dt / substeps
+    out = [(0, [(0, dts / 2.0)])]
+    for st in range(S):
+        k = st // substeps
+        out.append((1, [(k, dts)]))
+        if st + 1 < S:
+            out.append((0, [(k, dts / 2.0), ((st + 1) // substeps, dts / 2.0)]))
+    out.append((0, [(K - 1, dts / 2.0)]))
+    return out
+
+
+def schedule(pb: "Problem"):
+    """[(parity, factors)] of the truncated layers; ``factors(b)`` lists the
+    (kind, k, tau) factors of bond b's gate, first in time first.  Kinds:
+    "bond" = exp(-i tau h_b) with h_b of ``oracle.gates``; "V" = the
+    interaction c ZZ + J^x XX + J^y YY alone; "xl", "yl", "xr", "yr" = the
+    rotation exp(-i tau x X) (or y Y) of the bond's left or right site."""
+    if pb.order == 2:
+        return [(par, (lambda b, g=group: [("bond", k, tau) for (k, tau) in g]))
+                for (par, group) in merged_layers(pb.K, pb.dt, pb.substeps)]
+    if pb.order != 1:
+        raise ValueError("order must be 1 or 2")
+    N = pb.N
+    dts = pb.dt / pb.substeps
+    out = []
+    for st in range(pb.K * pb.substeps):
+        k = st // pb.substeps
+
+        def odd(b, k=k):
+            f = [("V", k, dts)]
+            if N % 2 == 1 and b == N - 2:   # the last site of an odd chain
+                f += [("yr", k, dts), ("xr", k, dts)]
+            return f
+
+        def even(b, k=k):
+            return [("V", k, dts), ("yl", k, dts), ("yr", k, dts), ("xl", k, dts), ("xr", k, dts)]
+
+        out.append((1, odd))
+        out.append((0, even))
     return out
 
 
@@ -112,6 +165,42 @@ def bond_gate(pb: Problem, s, k, b, tau):
     return _g.expm_hermitian(h, tau)
 
 
+_SINGLE = {"xl": (0, 0, "X"), "yl": (1, 0, "Y"), "xr": (0, 1, "X"), "yr": (1, 1, "Y")}
+
+
+def factor_hamiltonian(pb: Problem, s, b, kind, k):
+    """4x4 Hermitian h of one factor exp(-i tau h) of bond b's gate (see
+    ``schedule``)."""
+    if kind == "bond":
+        return _g.bond_hamiltonian(pb.N, b, *bond_params(pb, s, k, b))
+    xl, yl, xr, yr, c, jx, jy = bond_params(pb, s, k, b)
+    if kind == "V":
+        return c * np.kron(_g.Z, _g.Z) + jx * np.kron(_g.X, _g.X) + jy * np.kron(_g.Y, _g.Y)
+    amp = {"xl": xl, "yl": yl, "xr": xr, "yr": yr}[kind]
+    return amp * factor_generator(kind)
+
+
+def factor_generator(kind):
+    """d h / d amplitude of a single-site factor (X or Y on the left or right site)."""
+    _, side, op = _SINGLE[kind]
+    P = _g.X if op == "X" else _g.Y
+    return np.kron(P, _g.I2) if side == 0 else np.kron(_g.I2, P)
+
+
+def factor_params(pb: Problem, b, kind, k):
+    """[((k, c, i), dh/du)] for the controls that enter the factor."""
+    if kind == "bond":
+        gens = _g.bond_generators(pb.N, b)
+        return [(idx, gens[name]) for name, idx in param_slots(pb, k, b)]
+    if kind == "V":
+        if pb.C == 3 and pb.mask[2, b]:
+            return [((k, 2, b), np.kron(_g.Z, _g.Z))]
+        return []
+    c, side, _ = _SINGLE[kind]
+    i = b + side
+    return [((k, c, i), factor_generator(kind))] if pb.mask[c, i] else []
+
+
 def _layer_bonds(N, parity):
     return list(range(parity, N - 1, 2))
 
@@ -121,16 +210,17 @@ def trajectory(pb: Problem, s: int, p: int, want_grad: bool = True, stats=None):
     N = pb.N
     B, lam = _m.canonicalize(pb.inputs[p], pb.chi, pb.eps)
     T, tlam = _m.canonicalize(pb.targets[p], pb.chi, pb.eps)
-    sched = merged_layers(pb.K, pb.dt)
+    sched = schedule(pb)
     gate_cache = []
     hist = [([x.copy() for x in B], [x.copy() for x in lam])] if want_grad else None
-    for (par, group) in sched:
+    for (par, factors) in sched:
         gl = {}
         for b in _layer_bonds(N, par):
-            parts = [(k, tau) + bond_gate(pb, s, k, b, tau) for (k, tau) in group]
+            parts = [(kind, k, tau) + _g.expm_hermitian(factor_hamiltonian(pb, s, b, kind, k), tau)
+                     for (kind, k, tau) in factors(b)]
             Mg = np.eye(4, dtype=np.complex128)
             for part in parts:
-                Mg = part[2] @ Mg
+                Mg = part[3] @ Mg
             gl[b] = (Mg, parts)
             w, kk = _m.two_site_update(B, lam, b, Mg, pb.chi, pb.eps)
             if stats is not None:
@@ -145,19 +235,18 @@ def trajectory(pb: Problem, s: int, p: int, want_grad: bool = True, stats=None):
     dO = np.zeros((pb.K, pb.C, N), dtype=np.complex128)
     cB, clam = [x.copy() for x in T], [x.copy() for x in tlam]
     for li in range(len(sched) - 1, -1, -1):
-        par, group = sched[li]
+        par, _ = sched[li]
         a_after = hist[li + 1][0]
         for b in _layer_bonds(N, par):
             Mg, parts = gate_cache[li][b]
             rho = _m.mixed_two_site_density(cB, a_after, b)
-            gens = _g.bond_generators(N, b)
-            # gate j of the product M = G_n ... G_1:  dO/du = tr(Q_j L^dag rho L),
-            # Q_j = (dG_j/du) G_j^dag, L = G_n ... G_{j+1} (the gates after it)
+            # factor j of the product M = G_n ... G_1:  dO/du = tr(Q_j L^dag rho L),
+            # Q_j = (dG_j/du) G_j^dag, L = G_n ... G_{j+1} (the factors after it)
             Lt = np.eye(4, dtype=np.complex128)
-            for (k, tau, G, ev, V) in reversed(parts):
+            for (kind, k, tau, G, ev, V) in reversed(parts):
                 r = Lt.conj().T @ rho @ Lt
-                for name, idx in param_slots(pb, k, b):
-                    dG = _g.dexpm_hermitian(ev, V, tau, gens[name])
+                for idx, gen in factor_params(pb, b, kind, k):
+                    dG = _g.dexpm_hermitian(ev, V, tau, gen)
                     Q = dG @ G.conj().T
                     dO[idx] += np.trace(Q @ r)
                 Lt = Lt @ G
@@ -191,7 +280,7 @@ def from_workload(prob: dict, J: np.ndarray, g_fixed=None) -> Problem:
     return Problem(N=w.N, K=w.K, dt=w.dt, C=w.C, chi=w.chi, u=prob["u"], mask=prob["mask"],
                    J=J, inputs=[m.sites for m in prob["inputs"]],
                    targets=[m.sites for m in prob["targets"]], g_fixed=g_fixed,
-                   eps=w.sv_cutoff)
+                   eps=w.sv_cutoff, order=getattr(w, "order", 2), substeps=getattr(w, "substeps", 1))
 
 
 def per_gate_infidelity(chi_bar: float, n: int, qubits_per_gate: int) -> float:

@@ -263,6 +263,8 @@ class Workload:
     sv_cutoff: float = 1e-12
     u_sigma: float = 0.5
     crosstalk: int = 1       # 1: ZZ (J^z); 3: J^x XX + J^y YY + J^z ZZ (Eq. Hp)
+    order: int = 2           # Trotter order: 2 (A B A) or 1 (the slice of Eq. circuit)
+    substeps: int = 1        # Trotter steps per control bin
 
     @property
     def trajectories(self) -> int:

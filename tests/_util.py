@@ -13,13 +13,14 @@ TOL_O = 1e-10          # per-trajectory overlap
 def oracle_problem(w, u, mask, J, inputs, targets, g_fixed=None):
     return robust.Problem(N=w.N, K=w.K, dt=w.dt, C=w.C, chi=w.chi, u=u, mask=mask, J=J,
                           inputs=[m.sites for m in inputs], targets=[m.sites for m in targets],
-                          g_fixed=g_fixed, eps=w.sv_cutoff)
+                          g_fixed=g_fixed, eps=w.sv_cutoff, order=w.order, substeps=w.substeps)
 
 
-def gpu_context(w, inputs, targets, mask, g_fixed=None, checkpoint_every=0):
+def gpu_context(w, inputs, targets, mask, g_fixed=None, checkpoint_every=0, warps=0, ctas_per_sm=0):
     from paper_2603_03639_gb300 import Context
     return Context(w.N, w.K, w.dt, w.chi, w.M, w.C, inputs, targets, cutoff=w.sv_cutoff, mask=mask,
-                   g_fixed=g_fixed, checkpoint_every=checkpoint_every, crosstalk=w.crosstalk)
+                   g_fixed=g_fixed, checkpoint_every=checkpoint_every, crosstalk=w.crosstalk, warps=warps,
+                   ctas_per_sm=ctas_per_sm)
 
 
 def case(w, u=None):

@@ -18,10 +18,11 @@ PY = np.array([[0, -1j], [1j, 0]])
 PZ = np.diag([1.0, -1.0]).astype(complex)
 
 
-def mkpb(N, K, dt, C, chi, u, mask, J, inputs, targets, g_fixed=None, eps=1e-12):
-    return robust.Problem(N=N, K=K, dt=dt, C=C, chi=chi, u=u, mask=mask, J=np.atleast_2d(J),
+def mkpb(N, K, dt, C, chi, u, mask, J, inputs, targets, g_fixed=None, eps=1e-12, order=2, substeps=1):
+    return robust.Problem(N=N, K=K, dt=dt, C=C, chi=chi, u=u, mask=mask,
+                          J=np.atleast_2d(J) if np.ndim(J) < 3 else J,
                           inputs=[m.sites for m in inputs], targets=[m.sites for m in targets],
-                          g_fixed=g_fixed, eps=eps)
+                          g_fixed=g_fixed, eps=eps, order=order, substeps=substeps)
 
 
 def rand_products(N, P, seed):
@@ -320,6 +321,159 @@ def test_heisenberg_crosstalk_mps_equals_dense_and_fd():
         Fp, _, _ = robust.ensemble(mkpb(N, K, dt, 3, 8, up, mask, J, ins, tgs), want_grad=False)
         Fm, _, _ = robust.ensemble(mkpb(N, K, dt, 3, 8, um, mask, J, ins, tgs), want_grad=False)
         assert abs((Fp - Fm) / (2 * h) - g[idx]) < 1e-6 * max(1e-3, np.max(np.abs(g)))
+
+
+# ------------------------------------------- first-order split (Eq. circuit)
+def test_first_order_pi_pulse_gives_parallel_x():
+    # Eq. circuit with x = pi/(2T), y = 0, no crosstalk: every site gets exp(-i pi X / 2) = -iX
+    N, K, dt = 5, 8, 0.1
+    u = synth.pi_pulse_controls(K, 2, N, dt)
+    ins = rand_products(N, 2, 7)
+    pb = mkpb(N, K, dt, 2, 16, u, synth.control_mask(2, N), np.zeros(N - 1), ins, synth.x_targets(ins),
+              order=1, substeps=2)
+    F, g, _ = robust.ensemble(pb)
+    assert abs(F - 1.0) < 1e-13 and np.max(np.abs(g)) < 1e-12
+
+
+@pytest.mark.parametrize("substeps", [1, 3])
+def test_first_order_zero_crosstalk_closed_form(substeps):
+    """No interaction: each site evolves by prod_k (e^{-i d x X} e^{-i d y Y})^n_sub,
+    d = dt / n_sub -- X applied after Y, as the left-to-right order of Eq. circuit
+    says -- a product of 2x2 rotations with closed-form derivatives."""
+    N, K, dt = 5, 4, 0.15
+    rng = np.random.default_rng(41)
+    u = rng.normal(0, 0.8, size=(K, 2, N))
+    ins = rand_products(N, 1, 42)
+    tgs = rand_products(N, 1, 43)
+    pb = mkpb(N, K, dt, 2, 8, u, synth.control_mask(2, N), np.zeros(N - 1), ins, tgs, order=1,
+              substeps=substeps)
+    F, g, _ = robust.ensemble(pb)
+    d = dt / substeps
+
+    def rx(x):
+        return math.cos(d * x) * I2 - 1j * math.sin(d * x) * PX
+
+    def ry(y):
+        return math.cos(d * y) * I2 - 1j * math.sin(d * y) * PY
+
+    vin = [q.reshape(2) for q in ins[0].sites]
+    vt = [q.reshape(2) for q in tgs[0].sites]
+    Os, dOs = [], []
+    for i in range(N):
+        steps = [(k, rx(u[k, 0, i]) @ ry(u[k, 1, i])) for k in range(K) for _ in range(substeps)]
+        U = I2.astype(complex)
+        for _, S in steps:
+            U = S @ U
+        Os.append(np.vdot(vt[i], U @ vin[i]))
+        dd = np.zeros((K, 2), dtype=complex)
+        for j, (k, S) in enumerate(steps):
+            before = I2.astype(complex)
+            for _, S2 in steps[:j]:
+                before = S2 @ before
+            after = I2.astype(complex)
+            for _, S2 in steps[j + 1:]:
+                after = S2 @ after
+            x, y = u[k, 0, i], u[k, 1, i]
+            dSx = (-1j * d * PX) @ rx(x) @ ry(y)
+            dSy = rx(x) @ (-1j * d * PY) @ ry(y)
+            dd[k, 0] += np.vdot(vt[i], after @ dSx @ before @ vin[i])
+            dd[k, 1] += np.vdot(vt[i], after @ dSy @ before @ vin[i])
+        dOs.append(dd)
+    O = np.prod(Os)
+    assert abs(F - abs(O) ** 2) < 1e-13
+    gref = np.zeros((K, 2, N))
+    for i in range(N):
+        rest = np.prod([Os[j] for j in range(N) if j != i])
+        gref[:, :, i] = 2 * np.real(np.conj(O) * rest * dOs[i])
+    assert np.max(np.abs(g - gref)) < 1e-12 * max(1.0, np.max(np.abs(gref)))
+
+
+@pytest.mark.parametrize("N,terms,substeps", [(6, 1, 1), (5, 1, 2), (6, 3, 2), (5, 3, 1), (2, 1, 1)])
+def test_first_order_mps_equals_literal_circuit(N, terms, substeps):
+    """The folded truncated layers of the MPS path against Eq. circuit applied
+    gate by gate to a dense vector (every bond, then Y on every site, then X on
+    every site), untruncated: overlaps and costate gradients to 1e-12."""
+    K, dt = 3, 0.2
+    rng = np.random.default_rng(51 + N + terms)
+    u = rng.normal(0, 0.7, size=(K, 3, N))
+    mask = synth.control_mask(3, N, "all")
+    J = noise.sample_J(9, 2, N, 0, 0.3, terms=terms)
+    ins = rand_products(N, 2, 52)
+    tgs = rand_products(N, 2, 53)
+    pb = mkpb(N, K, dt, 3, 16, u, mask, J, ins, tgs, order=1, substeps=substeps)
+    for s in range(2):
+        for p in range(2):
+            o1, d1 = robust.trajectory(pb, s, p)
+            o2, d2 = dense.first_order_trajectory(pb, s, p)
+            assert abs(o1 - o2) < 1e-12
+            assert np.max(np.abs(d1 - d2)) < 1e-12
+
+
+def test_first_order_gradient_matches_finite_differences():
+    N, K, dt = 5, 3, 0.2
+    rng = np.random.default_rng(61)
+    u = rng.normal(0, 0.7, size=(K, 3, N))
+    mask = synth.control_mask(3, N, "all")
+    J = noise.sample_J(3, 2, N, 0, 0.2, terms=3)
+    ins = rand_products(N, 1, 62)
+    tgs = rand_products(N, 1, 63)
+    kw = dict(order=1, substeps=2)
+    F, g, _ = robust.ensemble(mkpb(N, K, dt, 3, 16, u, mask, J, ins, tgs, **kw))
+    h = 1e-6
+    checked = 0
+    for _ in range(30):
+        idx = tuple(int(rng.integers(0, n)) for n in u.shape)
+        if not mask[idx[1], idx[2]]:
+            continue
+        up, um = u.copy(), u.copy()
+        up[idx] += h
+        um[idx] -= h
+        Fp, _, _ = robust.ensemble(mkpb(N, K, dt, 3, 16, up, mask, J, ins, tgs, **kw), want_grad=False)
+        Fm, _, _ = robust.ensemble(mkpb(N, K, dt, 3, 16, um, mask, J, ins, tgs, **kw), want_grad=False)
+        assert abs((Fp - Fm) / (2 * h) - g[idx]) < 1e-6 * max(1e-3, np.max(np.abs(g)))
+        checked += 1
+    assert checked >= 12
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_substeps_equal_repeated_bins(order):
+    """n Trotter steps per bin are the map of n consecutive bins of length dt/n
+    holding the same controls; the gradient of a bin is the sum over its copies."""
+    N, K, dt, n = 6, 3, 0.3, 2
+    rng = np.random.default_rng(71)
+    u = rng.normal(0, 0.7, size=(K, 3, N))
+    mask = synth.control_mask(3, N, "all")
+    J = rng.uniform(-0.2, 0.2, size=(1, N - 1))
+    ins = rand_products(N, 1, 72)
+    tgs = rand_products(N, 1, 73)
+    o1, d1 = robust.trajectory(mkpb(N, K, dt, 3, 16, u, mask, J, ins, tgs, order=order, substeps=n), 0, 0)
+    u2 = np.repeat(u, n, axis=0)
+    o2, d2 = robust.trajectory(mkpb(N, K * n, dt / n, 3, 16, u2, mask, J, ins, tgs, order=order), 0, 0)
+    assert abs(o1 - o2) < 1e-13
+    assert np.max(np.abs(d1 - d2.reshape(K, n, 3, N).sum(axis=1))) < 1e-13
+
+
+def test_first_order_schedule_folds_each_site_once():
+    """Every site's two rotations enter exactly one bond gate per Trotter step,
+    after every bond gate of that step that touches the site."""
+    for N in (2, 3, 6, 7):
+        pb = mkpb(N, 1, 0.1, 2, 4, np.zeros((1, 2, N)), synth.control_mask(2, N), np.zeros(N - 1),
+                  rand_products(N, 1, 1), rand_products(N, 1, 2), order=1)
+        seen = {j: [] for j in range(N)}
+        last_touch = {j: -1 for j in range(N)}
+        t = 0
+        for par, factors in robust.schedule(pb):
+            for b in range(par, N - 1, 2):
+                for kind, _, _ in factors(b):
+                    if kind == "V":
+                        for j in (b, b + 1):
+                            assert not seen[j], "bond gate after the site's rotations"
+                            last_touch[j] = t
+                    else:
+                        seen[b + (kind[1] == "r")].append(kind[0])
+                t += 1
+        for j in range(N):
+            assert seen[j] == ["y", "x"], (N, j, seen[j])
 
 
 # ----------------------------------------------------------------- invariants
