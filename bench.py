@@ -431,6 +431,46 @@ def serving_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def plain_arm(args, w):
+    """Plain vs batched on the same sample: the trajectory kernel with one CTA
+    (one trajectory at a time, no graph) against the persistent launch over
+    all SMs, both through tnrc_fidelity_grad, on the workload cut to
+    `--plain-samples` noise samples (all P inputs, all K slices).  Prints one
+    JSON line; the headline number is gpu_arm's."""
+    import torch
+
+    from paper_2603_03639_gb300 import Context, autotune
+
+    ws = w.replace(M=args.plain_samples)
+    ins, tgs = ws.states()
+    tuned = autotune.lookup(w.N, w.K, w.chi, w.M, w.P, w.C, grad=True)
+    out = {}
+    for mode in ("batched", "plain"):
+        if mode == "plain":
+            os.environ["TNRC_GRID"] = "1"
+        try:
+            ctx = Context(ws.N, ws.K, ws.dt, ws.chi, ws.M, ws.C, ins, tgs, cutoff=ws.sv_cutoff, mask=ws.mask(),
+                          warps=tuned[0], ctas_per_sm=tuned[1])
+        finally:
+            os.environ.pop("TNRC_GRID", None)
+        ctx.set_controls(ws.controls())
+        ctx.sample_noise(ws.seed_J, ws.noise_dist, ws.noise_scale)
+        ctx.fidelity_grad()                       # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F, _ = ctx.fidelity_grad()
+        secs = time.perf_counter() - t0
+        out[mode] = {"value": ws.slice_steps / secs, "s_per_eval": secs, "F": float(F)}
+        ctx.close()
+    line = {"metric": "plain (one CTA, one trajectory at a time) vs batched persistent launch", "unit": UNIT,
+            "workload": w.name, "sample": "M=%d noise samples x P=%d inputs x K=%d slices, fwd+adjoint"
+            % (ws.M, ws.P, ws.K), "batched": out["batched"], "plain": out["plain"],
+            "speedup": out["batched"]["value"] / out["plain"]["value"],
+            "results_identical": bool(out["batched"]["F"] == out["plain"]["F"]),
+            "launch_shape": {"warps_per_cta": tuned[0] or "default", "ctas_per_sm": tuned[1] or 1}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -442,6 +482,9 @@ def main():
     ap.add_argument("--serving", action="store_true", help="serving rate sweep (separate JSON line)")
     ap.add_argument("--rates", default="1,2,4")
     ap.add_argument("--requests", type=int, default=16)
+    ap.add_argument("--plain", action="store_true",
+                    help="plain (one CTA) vs batched launch on a sample of the workload (separate JSON line)")
+    ap.add_argument("--plain-samples", type=int, default=2)
     ap.add_argument("--set", action="append", default=[], metavar="KEY=VALUE",
                     help="override a workload field (profiling cases), e.g. --set K=10 --set M=19")
     args = ap.parse_args()
@@ -452,6 +495,8 @@ def main():
         w = w.replace(**{key: type(cur)(val)})
     if args.serving:
         serving_arm(args)
+    elif args.plain:
+        plain_arm(args, w)
     elif args.impl == "reference":
         reference_arm(args, w)
     else:

@@ -7,8 +7,8 @@
  *     F = 1/(M P) sum_{s,p} | <t_p | U^(s) | in_p> |^2          (Sec. II; F = 1 - infidelity)
  *
  * over M noise realisations s (Sec. II: J_b^(s) iid per bond) and P input /
- * target state pairs, with U^(s) the second-order TEBD evolution of K
- * piecewise-constant control slices (Sec. II, Eq. circuit) on a complex128
+ * target state pairs, with U^(s) the TEBD evolution of K piecewise-constant
+ * control slices (Sec. II, Eq. circuit; second or first order) on a complex128
  * matrix-product state truncated by SVD to bond dimension chi_max, and its
  * exact costate gradient dF/du with respect to every control amplitude
  * (App. A).
@@ -20,12 +20,21 @@
  *     (X / Y drives of site i), slot 2 (C = 3) = g_i, the tunable ZZ coupling
  *     of bond (i, i+1).  A slot whose control_mask entry is 0 is not a
  *     control: it does not enter the Hamiltonian and its gradient is 0.
- *   - Slice k applies A(dt/2) B(dt) A(dt/2): A = the gates exp(-i tau h_b) of
- *     all even bonds, B = of all odd bonds, with
+ *   - Slice (control bin) k of length dt holds n_sub = substeps Trotter steps
+ *     of length dts = dt / n_sub.  Second order (trotter_order 2, default):
+ *     each step applies A(dts/2) B(dts) A(dts/2): A = the gates exp(-i tau h_b)
+ *     of all even bonds, B = of all odd bonds, with
  *       h_b = (g_b + gfix_b + J^z_b) ZZ + J^x_b XX + J^y_b YY
  *             + wL (x_b X + y_b Y) (x) I + wR I (x) (x_{b+1} X + y_{b+1} Y),
  *     (J^x = J^y = 0 unless crosstalk_terms = 3),
- *     wL = 1 on bond 0 else 1/2, wR = 1 on bond N-2 else 1/2.
+ *     wL = 1 on bond 0 else 1/2, wR = 1 on bond N-2 else 1/2; the half steps
+ *     A that meet at a step boundary are applied as one gate.  First order
+ *     (trotter_order 1, the slice of Eq. circuit): each step applies
+ *     exp(-i dts V_b) on every bond (odd bonds, then even bonds;
+ *     V_b = (g_b + gfix_b + J^z_b) ZZ + J^x_b XX + J^y_b YY), then
+ *     exp(-i dts y_i Y) and then exp(-i dts x_i X) on every site; each site's
+ *     rotations are applied together with the last bond gate of the step that
+ *     touches the site.
  *   - Truncation: after every two-site gate keep the
  *     k = min(chi_max, #{sigma_i > max(sv_cutoff, 1e-13) sigma_1}) largest
  *     singular values (at least one) and renormalise them to unit norm.
@@ -84,13 +93,16 @@ typedef struct {
   const uint8_t* control_mask;   /* [C][N], 1 = control; NULL = all x, y (and g on bonds)  */
   const double* g_fixed;         /* [K][N-1] fixed ZZ added on every bond, or NULL         */
   int32_t checkpoint_every;      /* slices per backward segment when the forward history is
-                                    recomputed; 0 = about sqrt(2K+1) layers                 */
+                                    recomputed; 0 = about sqrt(layers) truncated layers      */
   int32_t warps_per_cta;         /* trajectory-kernel warps per CTA, 2..8; 0 = default      */
-  int32_t ctas_per_sm;           /* resident trajectory CTAs per SM, 1..4 with
-                                    warps_per_cta * ctas_per_sm <= 8; 0 = 1                */
+  int32_t ctas_per_sm;           /* resident trajectory CTAs per SM, 1..4, clamped to
+                                    warps_per_cta * ctas_per_sm <= 16; above 8 warps per SM
+                                    the kernel's 128-register build runs; 0 = 1             */
   int32_t crosstalk_terms;       /* 1 (or 0): J^z ZZ per bond, J[M][N-1]; 3: the Heisenberg
                                     type J^x XX + J^y YY + J^z ZZ of Eq. Hp, J[M][N-1][3]
                                     in the order (x, y, z)                                 */
+  int32_t trotter_order;         /* 2 (or 0): A(dts/2) B(dts) A(dts/2); 1: Eq. circuit      */
+  int32_t substeps;              /* Trotter steps per slice, >= 1 (0 = 1)                   */
 } tnrc_problem;
 
 /* Per-call statistics of the last tnrc_fidelity / tnrc_fidelity_grad. */

@@ -18,8 +18,8 @@ import sys
 
 import numpy as np
 
-CANDIDATES = [(8, 1), (6, 1), (5, 1), (4, 2), (4, 1), (3, 2), (2, 4)]
-QUICK = [(8, 1), (6, 1), (4, 2), (3, 2)]
+CANDIDATES = [(8, 1), (6, 1), (5, 1), (4, 2), (4, 1), (3, 2), (2, 4), (8, 2), (4, 4), (6, 2), (5, 3)]
+QUICK = [(8, 1), (4, 2), (3, 2), (8, 2), (4, 4)]
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
 
@@ -63,7 +63,7 @@ def tune(N, K, dt, chi, M, C, inputs, targets, u, noise, mask=None, grad=True, c
     nb = max((N - 1 + 1) // 2, 1)
     times = {}
     for w, c in candidates:
-        if w * c > 8 or w > max(2, nb):
+        if w * c > 16 or w > max(2, nb):
             continue
         with Context(N, K, dt, chi, M, C, inputs, targets, mask=mask, stream=stream, warps=w, ctas_per_sm=c) as ctx:
             ctx.set_controls(u)

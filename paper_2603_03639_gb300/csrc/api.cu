@@ -16,9 +16,11 @@
 extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, size_t smem, cudaStream_t st);
 extern "C" cudaError_t tnrc_traj_prepare();
 extern "C" size_t tnrc_traj_smem(int warps, int slab_elems);
-extern "C" cudaError_t tnrc_launch_gates(int N, int K, int C, int M, int terms, double dt, const double* u,
-                                         const unsigned char* mask, const double* gfix, const double* J,
-                                         tnrc::GateEntry* out, double2* merged, int* status, cudaStream_t st);
+extern "C" cudaError_t tnrc_launch_layer_gates(int N, int K, int C, int M, int terms, int order, int nsub,
+                                               int L, int R, int first_parity, double dt, const double* u,
+                                               const unsigned char* mask, const double* gfix, const double* J,
+                                               const int* layer_off, tnrc::LayerGate* out, int* status,
+                                               cudaStream_t st);
 extern "C" cudaError_t tnrc_launch_noise(unsigned long long seed, int dist, double scale, int M, int nb, double* J,
                                          cudaStream_t st);
 extern "C" cudaError_t tnrc_launch_reduce(const double2* O, int T, double* F, double* per_traj, const double* gsp,
@@ -65,8 +67,11 @@ Layout make_layout(int N, int cap) {
 
 struct Plan {
   int N, K, C, chi, M, P, T, terms;
+  int order, nsub;            // Trotter order (1 or 2), Trotter steps per control bin
+  int n_layers, first_parity, recs;   // truncated layers, parity of layer 0, layer-gate records per sample
+  std::vector<int> layer_off; // [n_layers + 1] first record of each layer within a sample
   int seg, nseg;
-  int warps, slab_elems;
+  int warps, slab_elems, min_blocks;
   int grid;
   std::vector<int> dcap;      // [N+1] capacity of D[i]
   std::vector<int> site_off;  // [N]
@@ -75,7 +80,7 @@ struct Plan {
   int64_t work_stride;        // bytes per CTA
   int64_t env_elems;          // per CTA
   // arena offsets (bytes)
-  int64_t off_merged;
+  int64_t off_loff;
   int64_t off_u, off_mask, off_gfix, off_J, off_gates, off_in, off_tg, off_work, off_scratch, off_env, off_O,
       off_gsp, off_disc, off_counters, off_status, off_wc, off_F, off_grad, off_per, off_siteoff, off_dcap, total;
 };
@@ -98,9 +103,25 @@ bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, boo
   P.P = pb->n_inputs;
   P.T = (int)T;
   P.terms = pb->crosstalk_terms == 3 ? 3 : 1;
-  // checkpoint segments in truncated layers (2K+1 of them; 2 per slice)
-  const int L = 2 * K + 1;
-  P.seg = pb->checkpoint_every > 0 ? std::min(2 * pb->checkpoint_every, L) : (int)std::ceil(std::sqrt((double)L));
+  if (pb->trotter_order < 0 || pb->trotter_order > 2 || pb->substeps < 0) return false;
+  P.order = pb->trotter_order == 1 ? 1 : 2;
+  P.nsub = pb->substeps > 0 ? pb->substeps : 1;
+  if ((long long)K * P.nsub > (1 << 20)) return false;
+  // truncated layers: 2S+1 (second order; A half steps merged at step
+  // boundaries) or 2S (first order), S = K n_sub Trotter steps; parities alternate
+  const int S = K * P.nsub;
+  P.n_layers = (P.order == 2) ? 2 * S + 1 : 2 * S;
+  P.first_parity = (P.order == 2) ? 0 : 1;
+  P.layer_off.assign(P.n_layers + 1, 0);
+  for (int l = 0; l < P.n_layers; ++l) {
+    const int par = (l + P.first_parity) & 1;
+    P.layer_off[l + 1] = P.layer_off[l] + (N - 1 - par + 1) / 2;
+  }
+  P.recs = P.layer_off[P.n_layers];
+  // checkpoint segments in truncated layers
+  const int L = P.n_layers;
+  P.seg = pb->checkpoint_every > 0 ? (int)std::min<long long>(2ll * P.nsub * pb->checkpoint_every, L)
+                                   : (int)std::ceil(std::sqrt((double)L));
   P.nseg = (L + P.seg - 1) / P.seg;
   {
     Layout Y = make_layout(N, chi);
@@ -118,8 +139,11 @@ bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, boo
     const int w = atoi(e);
     if (w >= 2 && w <= tnrc::kWarps) P.warps = w;
   }
-  // the register file holds 8 warps of this kernel per SM
-  const int ctas_per_sm = std::max(1, std::min(pb->ctas_per_sm > 0 ? pb->ctas_per_sm : 1, tnrc::kWarps / P.warps));
+  // the register file holds 8 warps of the 255-register build per SM and 16 of
+  // the 128-register build; more than 8 warps per SM select the latter
+  const int ctas_per_sm =
+      std::max(1, std::min(pb->ctas_per_sm > 0 ? pb->ctas_per_sm : 1, 2 * tnrc::kWarps / P.warps));
+  P.min_blocks = (P.warps * ctas_per_sm > tnrc::kWarps) ? 2 : 1;
   // each warp's shared slab holds theta^dagger up to slab_elems complex values
   // (wider thetas use global scratch): split what the resident CTAs of an SM
   // leave after the per-warp arrays, within the 227 KB a CTA may use
@@ -151,8 +175,8 @@ bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, boo
   P.off_mask = take((int64_t)P.C * N);
   P.off_gfix = take((int64_t)K * (N - 1) * 8);
   P.off_J = take((int64_t)P.M * (N - 1) * P.terms * 8);
-  P.off_gates = take((int64_t)P.M * K * (N - 1) * sizeof(tnrc::GateEntry));
-  P.off_merged = take((int64_t)P.M * std::max(K - 1, 1) * (N - 1) * 16 * 16);
+  P.off_gates = take((int64_t)P.M * P.recs * (int64_t)sizeof(tnrc::LayerGate));
+  P.off_loff = take((int64_t)(P.n_layers + 1) * 4);
   P.off_in = take((int64_t)P.P * P.L.bytes);
   P.off_tg = take((int64_t)P.P * P.L.bytes);
   P.off_O = take(T * 16);
@@ -245,11 +269,10 @@ tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, dou
   if (!capturing) CK(cudaEventRecord(ctx->ev0, st));
   ctx->timed_last = !capturing;
   if (ctx->gates_dirty) {
-    CK(tnrc_launch_gates(P.N, P.K, P.C, P.M, P.terms, ctx->dt, ctx->at<double>(P.off_u),
-                         ctx->at<unsigned char>(P.off_mask),
-                         ctx->at<double>(P.off_gfix), ctx->at<double>(P.off_J),
-                         ctx->at<tnrc::GateEntry>(P.off_gates), ctx->at<double2>(P.off_merged),
-                         ctx->at<int>(P.off_status), st));
+    CK(tnrc_launch_layer_gates(P.N, P.K, P.C, P.M, P.terms, P.order, P.nsub, P.n_layers, P.recs, P.first_parity,
+                               ctx->dt, ctx->at<double>(P.off_u), ctx->at<unsigned char>(P.off_mask),
+                               ctx->at<double>(P.off_gfix), ctx->at<double>(P.off_J), ctx->at<int>(P.off_loff),
+                               ctx->at<tnrc::LayerGate>(P.off_gates), ctx->at<int>(P.off_status), st));
     ctx->gates_dirty = false;
   }
   CK(cudaMemsetAsync(ctx->at<int>(P.off_wc), 0, sizeof(int), st));
@@ -267,6 +290,7 @@ tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, dou
   tp.want_grad = grad ? 1 : 0;
   tp.warps = P.warps;
   tp.slab_elems = P.slab_elems;
+  tp.min_blocks = P.min_blocks;
   tp.full.L = P.L;
   tp.full.site_off = ctx->at<int>(P.off_siteoff);
   tp.full.dcap = ctx->at<int>(P.off_dcap);
@@ -281,8 +305,11 @@ tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, dou
   tp.warp_scratch = ctx->at<double2>(P.off_scratch);
   tp.scratch_elems = P.scratch_elems;
   tp.env_scratch = ctx->at<double2>(P.off_env);
-  tp.gates = ctx->at<tnrc::GateEntry>(P.off_gates);
-  tp.merged = ctx->at<double2>(P.off_merged);
+  tp.lgates = ctx->at<tnrc::LayerGate>(P.off_gates);
+  tp.layer_off = ctx->at<int>(P.off_loff);
+  tp.n_layers = P.n_layers;
+  tp.first_parity = P.first_parity;
+  tp.recs_per_sample = P.recs;
   tp.mask = ctx->at<unsigned char>(P.off_mask);
   tp.O = ctx->at<double2>(P.off_O);
   tp.gsp = ctx->at<double>(P.off_gsp);
@@ -448,6 +475,8 @@ tnrc_status tnrc_create(const tnrc_problem* pb, const tnrc_mps* inputs, const tn
           cudaSuccess ||
       cudaMemcpyAsync(ctx->at<void>(P.off_dcap), P.dcap.data(), (size_t)(N + 1) * 4, cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
+      cudaMemcpyAsync(ctx->at<void>(P.off_loff), P.layer_off.data(), (size_t)(P.n_layers + 1) * 4,
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemsetAsync(ctx->at<void>(P.off_status), 0, 16, st) != cudaSuccess ||
       cudaMemsetAsync(ctx->at<void>(P.off_in), 0, (size_t)P.P * P.L.bytes, st) != cudaSuccess ||
       cudaMemsetAsync(ctx->at<void>(P.off_tg), 0, (size_t)P.P * P.L.bytes, st) != cudaSuccess)

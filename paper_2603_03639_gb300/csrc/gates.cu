@@ -1,15 +1,23 @@
-// Bond gates of the second-order TEBD slice, and the noise realisations.
+// Layer gate table of the truncated TEBD layers, and the noise realisations.
 //
-// gate_kernel: one thread per (sample s, slice k, bond b).  Builds the bond
-// Hamiltonian of Eq. sysH with ZZ crosstalk,
-//   h = c ZZ + wL (x_b X + y_b Y) (x) I + wR I (x) (x_{b+1} X + y_{b+1} Y),
-//   c = g_b (if a control) + gfix_{k,b} + J^z(s)_b, plus J^x XX + J^y YY for
-//   the Heisenberg-type crosstalk of Eq. Hp,
-// diagonalises it by cyclic complex Jacobi rotations (FP64), and stores
-//   G = V e^{-i tau Lam} V^dag            (tau = dt/2 on even bonds, dt on odd)
-//   Gam_jk = -i tau e^{-i tau (l_j + l_k)/2} sinc(tau (l_j - l_k)/2)
-// (the divided differences of x -> e^{-i tau x}, used by the Daleckii-Krein
-// derivative of the gate in the gradient), and E_j = e^{-i tau l_j}.
+// layer_gate_kernel: one thread per (sample s, truncated layer l, bond b of
+// that layer).  The layer's gate on bond b is a product of factors
+// exp(-i tau h_f) (time order f = 1..F), each h_f Hermitian and linear in the
+// controls it contains:
+//   second order  (A(dts/2) B(dts) A(dts/2) per Trotter step, dts = dt/n_sub):
+//     one factor h_b = c ZZ + J^x XX + J^y YY + wL (x_b X + y_b Y) (x) I
+//                      + wR I (x) (x_{b+1} X + y_{b+1} Y)          (Eq. sysH, Eq. Hp)
+//     with tau = dts (odd bonds) or dts/2 (even bonds), or two such half-step
+//     factors where a step boundary merges them;
+//   first order   (Eq. circuit): the interaction c ZZ + J^x XX + J^y YY with
+//     tau = dts, followed on the bond that carries them by the single-site
+//     rotations y Y then x X of its sites;
+// c = g_b (if a control) + gfix_{k,b} + J^z(s)_b.  Each factor is diagonalised
+// by cyclic complex Jacobi rotations (FP64); the gate is the product and, for
+// every control u, Q_u = sum_f L_f (dG_f/du) G_f^dag L_f^dag (L_f the factors
+// after f) with dG_f/du by the Daleckii-Krein formula
+//   dG = V (Gam o (V^dag P V)) V^dag,  Gam_jk = -i tau e^{-i tau (l_j + l_k)/2} sinc(tau (l_j - l_k)/2),
+// P = dh_f/du.  The trajectory kernel then needs only tr(Q_u rho) per control.
 //
 // noise_kernel: J^(s)_b from the counter-based SplitMix64 generator (Steele,
 // Lea, Flood 2014): out(i) = mix(seed + (i+1) * 0x9E3779B97F4A7C15).
@@ -68,80 +76,26 @@ __device__ __forceinline__ void herm_rotate(double2 (&h)[16], double2 (&V)[16], 
   h[q * 4 + q].y = 0.0;
 }
 
-struct GateArgs {
-  int N, K, C, M, terms;
-  double dt;
-  const double* u;            // [K][C][N]
-  const unsigned char* mask;  // [C][N]
-  const double* gfix;         // [K][N-1] or null
-  const double* J;            // [M][N-1][terms]: (J^z) or (J^x, J^y, J^z)
-  GateEntry* out;             // [M][K][N-1]
-  int* status;
-};
-
-__global__ void gate_kernel(GateArgs a) {
-  const int nb = a.N - 1;
-  const long long total = (long long)a.M * a.K * nb;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const int b = (int)(idx % nb);
-  const int k = (int)((idx / nb) % a.K);
-  const int s = (int)(idx / ((long long)nb * a.K));
-  const double* uk = a.u + (size_t)k * a.C * a.N;
-  const unsigned char* mk = a.mask;
-  const double xl = uk[b] * mk[b];
-  const double yl = uk[a.N + b] * mk[a.N + b];
-  const double xr = uk[b + 1] * mk[b + 1];
-  const double yr = uk[a.N + b + 1] * mk[a.N + b + 1];
-  const double* Jb = a.J + ((size_t)s * nb + b) * a.terms;
-  double c = Jb[a.terms - 1];
-  const double jx = (a.terms == 3) ? Jb[0] : 0.0;
-  const double jy = (a.terms == 3) ? Jb[1] : 0.0;
-  if (a.C == 3) c += uk[2 * a.N + b] * mk[2 * a.N + b];
-  if (a.gfix) c += a.gfix[(size_t)k * nb + b];
-  const double wl = (b == 0) ? 1.0 : 0.5;
-  const double wr = (b + 1 == a.N - 1) ? 1.0 : 0.5;
-  const double tau = (b & 1) ? a.dt : 0.5 * a.dt;
-
-  double2 h[16], V[16];
+// Hermitian 4x4 eigendecomposition h = V diag(lam) V^dag by cyclic Jacobi
+// rotations; h is overwritten.  Returns false if it did not converge.
+__device__ bool herm_eig4(double2 (&h)[16], double2 (&V)[16], double (&lam)[4]) {
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    h[i] = make_double2(0.0, 0.0);
-    V[i] = make_double2((i % 5 == 0) ? 1.0 : 0.0, 0.0);
-  }
-  // ZZ diagonal (+1, -1, -1, +1)
-  h[0].x = c;
-  h[5].x = -c;
-  h[10].x = -c;
-  h[15].x = c;
-  // left site: (xl X + yl Y) (x) I couples |0 s2> <-> |1 s2>; <0|.|1> = xl - i yl
-  const double2 lz = make_double2(wl * xl, -wl * yl);
-  const double2 rz = make_double2(wr * xr, -wr * yr);
-  for (int s2 = 0; s2 < 2; ++s2) {
-    h[(0 + s2) * 4 + (2 + s2)] = lz;
-    h[(2 + s2) * 4 + (0 + s2)] = cconj(lz);
-  }
-  for (int s1 = 0; s1 < 2; ++s1) {
-    h[(2 * s1) * 4 + (2 * s1 + 1)] = rz;
-    h[(2 * s1 + 1) * 4 + (2 * s1)] = cconj(rz);
-  }
-  // crosstalk J^x XX + J^y YY: <00|.|11> = jx - jy, <01|.|10> = jx + jy
-  h[0 * 4 + 3].x += jx - jy;
-  h[3 * 4 + 0].x += jx - jy;
-  h[1 * 4 + 2].x += jx + jy;
-  h[2 * 4 + 1].x += jx + jy;
+  for (int i = 0; i < 16; ++i) V[i] = make_double2((i % 5 == 0) ? 1.0 : 0.0, 0.0);
   double scale2 = 0.0;
 #pragma unroll
   for (int i = 0; i < 16; ++i) scale2 += cabs2(h[i]);
   const double stop2 = 1e-32 * scale2;
-  int sweep = 0;
-  for (; sweep < 30; ++sweep) {
+  bool ok = false;
+  for (int sweep = 0; sweep < 30; ++sweep) {
     double off2 = 0.0;
 #pragma unroll
     for (int p = 0; p < 4; ++p)
 #pragma unroll
       for (int q = p + 1; q < 4; ++q) off2 += cabs2(h[p * 4 + q]);
-    if (off2 <= stop2) break;
+    if (off2 <= stop2) {
+      ok = true;
+      break;
+    }
     herm_rotate(h, V, 0, 1);
     herm_rotate(h, V, 2, 3);
     herm_rotate(h, V, 0, 2);
@@ -149,59 +103,288 @@ __global__ void gate_kernel(GateArgs a) {
     herm_rotate(h, V, 0, 3);
     herm_rotate(h, V, 1, 2);
   }
-  if (sweep == 30) atomicOr(a.status, kStatusNoConverge);
-  double lam[4];
-  double2 E[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    lam[j] = h[j * 5].x;
-    double sn, cs;
-    sincos(tau * lam[j], &sn, &cs);
-    E[j] = make_double2(cs, -sn);
-  }
-  GateEntry& ge = a.out[idx];
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      double2 g = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) cfma(g, V[r * 4 + j], cmulc(E[j], V[cc * 4 + j]));
-      ge.G[r * 4 + cc] = g;
-      ge.V[r * 4 + cc] = V[r * 4 + cc];
-      // Gam_rc = -i tau e^{-i tau (l_r + l_c)/2} sinc(tau (l_r - l_c)/2)
-      const double x = 0.5 * tau * (lam[r] - lam[cc]);
-      const double sinc = (fabs(x) < 1e-8) ? 1.0 - x * x / 6.0 : sin(x) / x;
-      double sn, cs;
-      sincos(0.5 * tau * (lam[r] + lam[cc]), &sn, &cs);
-      // -i tau (cs - i sn) sinc = tau sinc (-sn - i cs)
-      ge.Gam[r * 4 + cc] = make_double2(-tau * sinc * sn, -tau * sinc * cs);
-    }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) ge.E[j] = E[j];
+  for (int j = 0; j < 4; ++j) lam[j] = h[j * 5].x;
+  return ok;
 }
 
-// Merged half-step gates of the even bonds: Gm[s][k][b] = G[s][k+1][b] G[s][k][b]
-// (k = 0..K-2), the A(dt/2) that ends slice k followed by the one that starts
-// slice k+1, applied as one gate before one truncation.
-__global__ void merge_kernel(int N, int K, int M, const GateEntry* g, double2* gm) {
-  const int nb = N - 1;
-  const int ne = (nb + 1) / 2;  // even bonds
-  const long long total = (long long)M * (K - 1) * ne * 16;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const int e = (int)(idx & 15);
-  const long long rest = idx >> 4;
-  const int b = 2 * (int)(rest % ne);
-  const int k = (int)((rest / ne) % (K - 1));
-  const int s = (int)(rest / ((long long)ne * (K - 1)));
-  const GateEntry& g1 = g[((size_t)s * K + k) * nb + b];
-  const GateEntry& g2 = g[((size_t)s * K + k + 1) * nb + b];
-  const int r = e >> 2, c = e & 3;
-  double2 acc = make_double2(0.0, 0.0);
+// Generators in the bond basis |s_b s_{b+1}> (index 2 s_b + s_{b+1}), scaled by w:
+// 0: X (x) I, 1: Y (x) I, 2: I (x) X, 3: I (x) Y, 4: Z (x) Z.
+__device__ void generator4(int code, double w, double2 (&P)[16]) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) cfma(acc, g2.G[r * 4 + j], g1.G[j * 4 + c]);
-  gm[(((size_t)s * (K - 1) + k) * nb + b) * 16 + e] = acc;
+  for (int i = 0; i < 16; ++i) P[i] = make_double2(0.0, 0.0);
+  switch (code) {
+    case 0:
+      P[0 * 4 + 2].x = w; P[1 * 4 + 3].x = w; P[2 * 4 + 0].x = w; P[3 * 4 + 1].x = w;
+      break;
+    case 1:
+      P[0 * 4 + 2].y = -w; P[1 * 4 + 3].y = -w; P[2 * 4 + 0].y = w; P[3 * 4 + 1].y = w;
+      break;
+    case 2:
+      P[0 * 4 + 1].x = w; P[1 * 4 + 0].x = w; P[2 * 4 + 3].x = w; P[3 * 4 + 2].x = w;
+      break;
+    case 3:
+      P[0 * 4 + 1].y = -w; P[1 * 4 + 0].y = w; P[2 * 4 + 3].y = -w; P[3 * 4 + 2].y = w;
+      break;
+    default:
+      P[0].x = w; P[5].x = -w; P[10].x = -w; P[15].x = w;
+      break;
+  }
+}
+
+struct LayerGateArgs {
+  int N, K, C, M, terms, order, nsub, L, R, first_parity;
+  double dt;
+  const double* u;            // [K][C][N]
+  const unsigned char* mask;  // [C][N]
+  const double* gfix;         // [K][N-1] or null
+  const double* J;            // [M][N-1][terms]: (J^z) or (J^x, J^y, J^z)
+  const int* layer_off;       // [L + 1]
+  LayerGate* out;             // [M][R]
+  int* status;
+};
+
+// factor kinds
+constexpr int kFBond = 0, kFInter = 1, kFXl = 2, kFYl = 3, kFXr = 4, kFYr = 5;
+constexpr int kMaxFactors = 5;
+
+__global__ void layer_gate_kernel(LayerGateArgs a) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)a.M * a.R) return;
+  const int s = (int)(idx / a.R);
+  const int r = (int)(idx - (long long)s * a.R);
+  int lo = 0, hi = a.L;  // largest l with layer_off[l] <= r
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (a.layer_off[mid] <= r) lo = mid; else hi = mid;
+  }
+  const int l = lo;
+  const int parity = (l + a.first_parity) & 1;
+  const int b = parity + 2 * (r - a.layer_off[l]);
+  const int N = a.N, nb = N - 1;
+  const int S = a.K * a.nsub;
+  const double dts = a.dt / a.nsub;
+
+  // the layer's factors on bond b, first in time first
+  int fk[kMaxFactors], fkind[kMaxFactors];
+  double ftau[kMaxFactors];
+  int nf = 0;
+  if (a.order == 2) {
+    if (l & 1) {
+      fkind[nf] = kFBond; fk[nf] = ((l - 1) >> 1) / a.nsub; ftau[nf++] = dts;
+    } else if (l == 0) {
+      fkind[nf] = kFBond; fk[nf] = 0; ftau[nf++] = 0.5 * dts;
+    } else if (l == 2 * S) {
+      fkind[nf] = kFBond; fk[nf] = (S - 1) / a.nsub; ftau[nf++] = 0.5 * dts;
+    } else {
+      const int st = (l >> 1) - 1;
+      fkind[nf] = kFBond; fk[nf] = st / a.nsub; ftau[nf++] = 0.5 * dts;
+      fkind[nf] = kFBond; fk[nf] = (st + 1) / a.nsub; ftau[nf++] = 0.5 * dts;
+    }
+  } else {
+    const int k = (l >> 1) / a.nsub;
+    fkind[nf] = kFInter; fk[nf] = k; ftau[nf++] = dts;
+    if (l & 1) {  // even bonds: both sites' rotations, Y before X
+      fkind[nf] = kFYl; fk[nf] = k; ftau[nf++] = dts;
+      fkind[nf] = kFYr; fk[nf] = k; ftau[nf++] = dts;
+      fkind[nf] = kFXl; fk[nf] = k; ftau[nf++] = dts;
+      fkind[nf] = kFXr; fk[nf] = k; ftau[nf++] = dts;
+    } else if ((N & 1) && b == N - 2) {  // the last site of an odd chain
+      fkind[nf] = kFYr; fk[nf] = k; ftau[nf++] = dts;
+      fkind[nf] = kFXr; fk[nf] = k; ftau[nf++] = dts;
+    }
+  }
+
+  const double* Jb = a.J + ((size_t)s * nb + b) * a.terms;
+  const double jz = Jb[a.terms - 1];
+  const double jx = (a.terms == 3) ? Jb[0] : 0.0;
+  const double jy = (a.terms == 3) ? Jb[1] : 0.0;
+  const double wl = (b == 0) ? 1.0 : 0.5;
+  const double wr = (b + 1 == N - 1) ? 1.0 : 0.5;
+
+  // eigendecomposition and exponential of every factor
+  double2 Vf[kMaxFactors][16], Gf[kMaxFactors][16];
+  double lamf[kMaxFactors][4];
+  for (int f = 0; f < nf; ++f) {
+    const int k = fk[f];
+    const double* uk = a.u + (size_t)k * a.C * N;
+    const unsigned char* mk = a.mask;
+    const double xl = uk[b] * mk[b];
+    const double yl = uk[N + b] * mk[N + b];
+    const double xr = uk[b + 1] * mk[b + 1];
+    const double yr = uk[N + b + 1] * mk[N + b + 1];
+    double c = jz;
+    if (a.C == 3) c += uk[2 * N + b] * mk[2 * N + b];
+    if (a.gfix) c += a.gfix[(size_t)k * nb + b];
+    double2 h[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) h[i] = make_double2(0.0, 0.0);
+    if (fkind[f] == kFBond || fkind[f] == kFInter) {
+      h[0].x = c;
+      h[5].x = -c;
+      h[10].x = -c;
+      h[15].x = c;
+      // J^x XX + J^y YY: <00|.|11> = jx - jy, <01|.|10> = jx + jy
+      h[0 * 4 + 3].x += jx - jy;
+      h[3 * 4 + 0].x += jx - jy;
+      h[1 * 4 + 2].x += jx + jy;
+      h[2 * 4 + 1].x += jx + jy;
+      if (fkind[f] == kFBond) {
+        // (x X + y Y) on a site couples |0> <-> |1> with <0|.|1> = x - i y
+        const double2 lz = make_double2(wl * xl, -wl * yl);
+        const double2 rz = make_double2(wr * xr, -wr * yr);
+        for (int q = 0; q < 2; ++q) {
+          h[(0 + q) * 4 + (2 + q)] = lz;
+          h[(2 + q) * 4 + (0 + q)] = cconj(lz);
+          h[(2 * q) * 4 + (2 * q + 1)] = rz;
+          h[(2 * q + 1) * 4 + (2 * q)] = cconj(rz);
+        }
+      }
+    } else {
+      const int code = fkind[f] - kFXl;  // 0 X(x)I, 1 Y(x)I, 2 I(x)X, 3 I(x)Y
+      const double amp = (code == 0) ? xl : (code == 1) ? yl : (code == 2) ? xr : yr;
+      generator4(code, amp, h);
+    }
+    if (!herm_eig4(h, Vf[f], lamf[f])) atomicOr(a.status, kStatusNoConverge);
+    double2 E[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      double sn, cs;
+      sincos(ftau[f] * lamf[f][j], &sn, &cs);
+      E[j] = make_double2(cs, -sn);
+    }
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        double2 g = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cfma(g, Vf[f][rr * 4 + j], cmulc(E[j], Vf[f][cc * 4 + j]));
+        Gf[f][rr * 4 + cc] = g;
+      }
+  }
+
+  // walk the factors backwards: Lt = product of the factors after f
+  LayerGate& out = a.out[idx];
+  double2 Lt[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) Lt[i] = make_double2((i % 5 == 0) ? 1.0 : 0.0, 0.0);
+  int nq = 0;
+  for (int f = nf - 1; f >= 0; --f) {
+    const int k = fk[f];
+    // the controls of this factor: (generator code, weight, c, site)
+    int pc[5], pcc[5], psite[5];
+    double pw[5];
+    int np = 0;
+    const unsigned char* mk = a.mask;
+    if (fkind[f] == kFBond) {
+      if (mk[b]) { pc[np] = 0; pw[np] = wl; pcc[np] = 0; psite[np++] = b; }
+      if (mk[N + b]) { pc[np] = 1; pw[np] = wl; pcc[np] = 1; psite[np++] = b; }
+      if (mk[b + 1]) { pc[np] = 2; pw[np] = wr; pcc[np] = 0; psite[np++] = b + 1; }
+      if (mk[N + b + 1]) { pc[np] = 3; pw[np] = wr; pcc[np] = 1; psite[np++] = b + 1; }
+    }
+    if ((fkind[f] == kFBond || fkind[f] == kFInter) && a.C == 3 && mk[2 * N + b]) {
+      pc[np] = 4; pw[np] = 1.0; pcc[np] = 2; psite[np++] = b;
+    }
+    if (fkind[f] >= kFXl) {
+      const int code = fkind[f] - kFXl;
+      const int cidx = code & 1, site = b + (code >> 1);
+      if (mk[cidx * N + site]) { pc[np] = code; pw[np] = 1.0; pcc[np] = cidx; psite[np++] = site; }
+    }
+    for (int q = 0; q < np; ++q) {
+      // Q_f = V (Gam o (V^dag P V)) e^{i tau Lam} V^dag  (= dG_f G_f^dag)
+      double2 P[16], T1[16], T2[16];
+      generator4(pc[q], pw[q], P);
+      const double tau = ftau[f];
+      const double* lam = lamf[f];
+      const double2* V = Vf[f];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)       // T1 = P V
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) cfma(acc, P[i * 4 + m], V[m * 4 + j]);
+          T1[i * 4 + j] = acc;
+        }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)       // T2 = (Gam o (V^dag T1)) e^{i tau Lam}
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) cfmac(acc, V[m * 4 + i], T1[m * 4 + j]);
+          const double x = 0.5 * tau * (lam[i] - lam[j]);
+          const double sinc = (fabs(x) < 1e-8) ? 1.0 - x * x / 6.0 : sin(x) / x;
+          double sn, cs;
+          sincos(0.5 * tau * (lam[i] + lam[j]), &sn, &cs);
+          // -i tau (cs - i sn) sinc = tau sinc (-sn - i cs); times e^{+i tau lam_j}
+          const double2 gam = make_double2(-tau * sinc * sn, -tau * sinc * cs);
+          double se, ce;
+          sincos(tau * lam[j], &se, &ce);
+          T2[i * 4 + j] = cmul(cmul(gam, acc), make_double2(ce, se));
+        }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)       // T1 = V T2 V^dag
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            double2 t = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int n2 = 0; n2 < 4; ++n2) cfma(t, T2[m * 4 + n2], cconj(V[j * 4 + n2]));
+            cfma(acc, V[i * 4 + m], t);
+          }
+          T1[i * 4 + j] = acc;
+        }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)       // T2 = Lt T1 Lt^dag
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            double2 t = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int n2 = 0; n2 < 4; ++n2) cfma(t, T1[m * 4 + n2], cconj(Lt[j * 4 + n2]));
+            cfma(acc, Lt[i * 4 + m], t);
+          }
+          T2[i * 4 + j] = acc;
+        }
+      const int slot = (k * a.C + pcc[q]) * N + psite[q];
+      int at = -1;
+      for (int e = 0; e < nq; ++e)
+        if (out.slot[e] == slot) at = e;
+      if (at < 0 && nq < kMaxLayerParams) {
+        at = nq++;
+        out.slot[at] = slot;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) out.Q[at][i] = T2[i];
+      } else if (at >= 0) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) out.Q[at][i] = make_double2(out.Q[at][i].x + T2[i].x, out.Q[at][i].y + T2[i].y);
+      } else {
+        atomicOr(a.status, kStatusBadDims);   // cannot happen: at most 10 distinct controls
+      }
+    }
+    // Lt <- Lt G_f
+    double2 T[16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) cfma(acc, Lt[i * 4 + m], Gf[f][m * 4 + j]);
+        T[i * 4 + j] = acc;
+      }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) Lt[i] = T[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) out.G[i] = Lt[i];
+  out.nq = nq;
 }
 
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long i) {
@@ -254,19 +437,18 @@ __global__ void reduce_grad_kernel(const double* gsp, int T, int X, double* grad
 
 }  // namespace tnrc
 
-extern "C" cudaError_t tnrc_launch_gates(int N, int K, int C, int M, int terms, double dt, const double* u,
-                                         const unsigned char* mask, const double* gfix, const double* J,
-                                         tnrc::GateEntry* out, double2* merged, int* status, cudaStream_t st) {
-  tnrc::GateArgs a{N, K, C, M, terms, dt, u, mask, gfix, J, out, status};
-  const long long total = (long long)M * K * (N - 1);
-  const int threads = 128;
+extern "C" cudaError_t tnrc_launch_layer_gates(int N, int K, int C, int M, int terms, int order, int nsub,
+                                               int L, int R, int first_parity, double dt, const double* u,
+                                               const unsigned char* mask, const double* gfix, const double* J,
+                                               const int* layer_off, tnrc::LayerGate* out, int* status,
+                                               cudaStream_t st) {
+  tnrc::LayerGateArgs a{N, K, C, M, terms, order, nsub, L, R, first_parity, dt, u, mask, gfix, J, layer_off, out,
+                        status};
+  const long long total = (long long)M * R;
+  const int threads = 64;
   const long long blocks = (total + threads - 1) / threads;
   (void)cudaGetLastError();  // report only this launch below
-  tnrc::gate_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);
-  if (K > 1) {
-    const long long tm = (long long)M * (K - 1) * (N / 2) * 16;
-    tnrc::merge_kernel<<<(unsigned)((tm + 255) / 256), 256, 0, st>>>(N, K, M, out, merged);
-  }
+  tnrc::layer_gate_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

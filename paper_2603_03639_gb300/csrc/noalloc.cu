@@ -31,9 +31,11 @@
 extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, size_t smem, cudaStream_t st);
 extern "C" cudaError_t tnrc_traj_prepare();
 extern "C" size_t tnrc_traj_smem(int warps, int slab_elems);
-extern "C" cudaError_t tnrc_launch_gates(int N, int K, int C, int M, int terms, double dt, const double* u,
-                                         const unsigned char* mask, const double* gfix, const double* J,
-                                         tnrc::GateEntry* out, double2* merged, int* status, cudaStream_t st);
+extern "C" cudaError_t tnrc_launch_layer_gates(int N, int K, int C, int M, int terms, int order, int nsub,
+                                               int L, int R, int first_parity, double dt, const double* u,
+                                               const unsigned char* mask, const double* gfix, const double* J,
+                                               const int* layer_off, tnrc::LayerGate* out, int* status,
+                                               cudaStream_t st);
 extern "C" cudaError_t tnrc_launch_reduce(const double2* O, int T, double* F, double* per_traj, const double* gsp,
                                           int X, double* grad, cudaStream_t st);
 extern "C" cudaError_t tnrc_launch_canon(const tnrc::CanonArgs* a, int nmps, cudaStream_t st);
@@ -82,6 +84,17 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
     return TNRC_E_INVALID;
   if (pb->crosstalk_terms != 0 && pb->crosstalk_terms != 1 && pb->crosstalk_terms != 3) return TNRC_E_INVALID;
   const int terms = pb->crosstalk_terms == 3 ? 3 : 1;
+  if (pb->trotter_order < 0 || pb->trotter_order > 2 || pb->substeps < 0) return TNRC_E_INVALID;
+  const int order = pb->trotter_order == 1 ? 1 : 2;
+  const int nsub = pb->substeps > 0 ? pb->substeps : 1;
+  if ((long long)K * nsub > (1 << 20)) return TNRC_E_INVALID;
+  // truncated layers (alternating bond parity) and their gate records per sample
+  const int S = K * nsub;
+  const int n_layers = (order == 2) ? 2 * S + 1 : 2 * S;
+  const int first_parity = (order == 2) ? 0 : 1;
+  std::vector<int> layer_off(n_layers + 1, 0);
+  for (int l = 0; l < n_layers; ++l) layer_off[l + 1] = layer_off[l] + (N - 1 - ((l + first_parity) & 1) + 1) / 2;
+  const int recs = layer_off[n_layers];
   if (!(pb->dt > 0.0) || !std::isfinite(pb->dt) || !(pb->sv_cutoff >= 0.0) || !(pb->sv_cutoff < 1.0))
     return TNRC_E_INVALID;
   const long long T = (long long)M * P;
@@ -146,8 +159,8 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
                 o_rdims = take((int64_t)rdims.size() * 4), o_roffs = take((int64_t)roffs.size() * 8),
                 o_raw = take(rtotal * 16), o_cwork = take((int64_t)2 * P * cwork * 16),
                 o_slots = take((int64_t)2 * P * L.bytes),
-                o_gates = take((int64_t)M * K * (N - 1) * sizeof(tnrc::GateEntry)),
-                o_merged = take((int64_t)M * std::max(K - 1, 1) * (N - 1) * 256), o_O = take(T * 16),
+                o_gates = take((int64_t)M * recs * (int64_t)sizeof(tnrc::LayerGate)),
+                o_loff = take((int64_t)(n_layers + 1) * 4), o_O = take(T * 16),
                 o_disc = take(T * 8), o_per = take(T * 8), o_small = take(4096);
   int maxb = 0;
   for (int par = 0; par < 2; ++par) maxb = std::max(maxb, (N - 1 - par + 1) / 2);
@@ -199,6 +212,8 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
             cudaMemcpyAsync(base + o_J, J, (size_t)M * (N - 1) * terms * 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(base + o_site, site_off.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(base + o_dcap, dcap.data(), (size_t)(N + 1) * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+            cudaMemcpyAsync(base + o_loff, layer_off.data(), layer_off.size() * 4, cudaMemcpyHostToDevice, st) ==
+                cudaSuccess &&
             cudaMemcpyAsync(base + o_rdims, rdims.data(), rdims.size() * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(base + o_roffs, roffs.data(), roffs.size() * 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(base + o_raw, raw.data(), raw.size() * 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
@@ -229,10 +244,11 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   ca.status = status;
   if (tnrc_launch_canon(&ca, 2 * P, st) != cudaSuccess) return TNRC_E_CUDA;
   // ---- gates ----
-  if (tnrc_launch_gates(N, K, C, M, terms, pb->dt, reinterpret_cast<const double*>(base + o_u), base + o_mask,
-                        reinterpret_cast<const double*>(base + o_gfix), reinterpret_cast<const double*>(base + o_J),
-                        reinterpret_cast<tnrc::GateEntry*>(base + o_gates),
-                        reinterpret_cast<double2*>(base + o_merged), status, st) != cudaSuccess)
+  if (tnrc_launch_layer_gates(N, K, C, M, terms, order, nsub, n_layers, recs, first_parity, pb->dt,
+                              reinterpret_cast<const double*>(base + o_u), base + o_mask,
+                              reinterpret_cast<const double*>(base + o_gfix),
+                              reinterpret_cast<const double*>(base + o_J), reinterpret_cast<const int*>(base + o_loff),
+                              reinterpret_cast<tnrc::LayerGate*>(base + o_gates), status, st) != cudaSuccess)
     return TNRC_E_CUDA;
   // ---- trajectories (forward and overlap only) ----
   tnrc::TrajParams tp{};
@@ -248,10 +264,11 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   tp.want_grad = 0;
   tp.warps = warps;
   tp.slab_elems = slab;
+  tp.min_blocks = 1;
   tp.full.L = L;
   tp.full.site_off = reinterpret_cast<const int*>(base + o_site);
   tp.full.dcap = reinterpret_cast<const int*>(base + o_dcap);
-  tp.full.seg = 2 * K + 1;
+  tp.full.seg = n_layers;
   tp.full.nseg = 1;
   tp.packed_history = 0;
   tp.history_cap = 0;
@@ -262,8 +279,11 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   tp.warp_scratch = reinterpret_cast<double2*>(base + o_wscr);
   tp.scratch_elems = scratch_elems;
   tp.env_scratch = reinterpret_cast<double2*>(base + o_env);
-  tp.gates = reinterpret_cast<const tnrc::GateEntry*>(base + o_gates);
-  tp.merged = reinterpret_cast<const double2*>(base + o_merged);
+  tp.lgates = reinterpret_cast<const tnrc::LayerGate*>(base + o_gates);
+  tp.layer_off = reinterpret_cast<const int*>(base + o_loff);
+  tp.n_layers = n_layers;
+  tp.first_parity = first_parity;
+  tp.recs_per_sample = recs;
   tp.mask = base + o_mask;
   tp.O = reinterpret_cast<double2*>(base + o_O);
   tp.gsp = nullptr;

@@ -55,11 +55,22 @@ struct SlotLayout {
   int64_t bytes;      // slot stride
 };
 
-struct GateEntry {    // one bond gate of one (sample, slice)
-  double2 G[16];      // exp(-i tau h) row-major, basis |s_b s_b+1>
-  double2 V[16];      // eigenvectors of h (columns)
-  double2 Gam[16];    // divided differences of exp(-i tau x) at the eigenvalues
-  double2 E[4];       // exp(-i tau lambda_j)
+// The gate of one bond in one truncated layer for one noise sample, with
+// what the costate gradient needs of it.  The gate is a product of factors
+// G = G_F ... G_1 (one factor, or the two half steps merged at a step
+// boundary, or the interaction and the folded single-site rotations of the
+// first-order slice); for every control u it depends on,
+//   Q_u = sum over the factors f containing u of L_f (dG_f/du) G_f^dag L_f^dag,
+//   L_f = G_F ... G_{f+1},
+// so that dO/du = tr(Q_u rho) with rho the mixed two-site density of the
+// costate and the state after the layer (App. A).
+constexpr int kMaxLayerParams = 10;
+struct LayerGate {
+  double2 G[16];                       // row-major, basis |s_b s_b+1>
+  double2 Q[kMaxLayerParams][16];      // row-major
+  int slot[kMaxLayerParams];           // gradient index k C N + c N + site
+  int nq;                              // number of controls the gate depends on
+  int pad_[5];
 };
 
 // One slot layout: byte layout, site offsets, capacities and the checkpoint
@@ -76,6 +87,8 @@ struct TrajParams {
   double dt, eps;              // eps = max(cutoff, kZeroFloor)
   int want_grad;
   int warps;                   // warps per CTA
+  int min_blocks;              // register budget of the launch: 1 = up to 8 warps per SM
+                               // (255 registers), 2 = up to 16 warps per SM (128 registers)
   int slab_elems;              // complex elements of each warp's shared slab
   Lay full;                    // capacities min(2^i, 2^(N-i), chi)
   int packed_history;          // keep the forward history packed (no recomputation)
@@ -87,8 +100,11 @@ struct TrajParams {
   double2* warp_scratch;           // per warp: scratch_elems complex
   int64_t scratch_elems;
   double2* env_scratch;            // per CTA: 2*(N+1)*chi*chi complex
-  const GateEntry* gates;          // [M][K][N-1]
-  const double2* merged;           // [M][K-1][N-1][16]: G[k+1] G[k] on even bonds
+  const LayerGate* lgates;         // [M][recs_per_sample]: layer l's bonds at layer_off[l]
+  const int* layer_off;            // [n_layers + 1]
+  int n_layers;                    // truncated layers of one trajectory
+  int first_parity;                // bond parity of layer 0 (they alternate)
+  int recs_per_sample;
   const unsigned char* mask;       // [C][N]
   double2* O;                      // [T]
   double* gsp;                     // [T][K*C*N] or null

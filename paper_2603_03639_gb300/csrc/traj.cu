@@ -1,18 +1,24 @@
 // Persistent trajectory kernel: one CTA evaluates one trajectory (noise sample
 // s, input p) at a time and takes the next one from a device work counter.
 //
-//   forward  (Sec. II, Eq. circuit): K slices of A(dt/2) B(dt) A(dt/2), applied
-//            as the 2K+1 truncated layers A_0, B_0, A_0A_1, B_1, ..., B_{K-1},
-//            A_{K-1} (the two half layers at a slice boundary merged into one
-//            gate: the state is compressed once per time step); every
-//            two-site gate is followed by the truncated SVD; the warps of the
-//            CTA take the disjoint bonds of a layer in a fixed round-robin.
+//   forward  (Sec. II): the truncated layers of the time discretisation, each
+//            a set of disjoint two-site gates with their parity alternating --
+//            for the second-order split A(dt/2) B(dt) A(dt/2) per Trotter step
+//            the 2S+1 layers A_0, B_0, A_0A_1, B_1, ..., B_{S-1}, A_{S-1} (half
+//            layers at a step boundary merged into one gate: the state is
+//            compressed once per time step), for the first-order slice of
+//            Eq. circuit two layers per step (odd bonds; even bonds with the
+//            single-site rotations folded in).  Every two-site gate is
+//            followed by the truncated SVD; the warps of the CTA share the
+//            disjoint bonds of a layer, largest first.
 //   overlap  (Sec. II state form): O = <t_p | a(T)> by a transfer-matrix sweep.
 //   gradient (App. A): the costate b_l = L_{l+1}^dag .. L_L^dag t is propagated
 //            backwards with the same truncated update; for every gate of layer
-//            l, dO/du += <b_l| (dG/du) G^dag |a_l> from the left/right
-//            environments of <b_l|.|a_l>; the forward states a_l are
-//            recomputed segment by segment from checkpoints every `seg` slices.
+//            l, dO/du += tr(Q_u rho) with rho the mixed two-site density of
+//            <b_l|.|a_l> from left/right environments and Q_u from the layer
+//            gate table; the forward states a_l come from the packed history
+//            of the forward pass (or are recomputed segment by segment from
+//            checkpoints when the history does not fit).
 // Each trajectory writes its own O and its own gradient row, so results do not
 // depend on which CTA ran it or on what else ran in the launch.
 #include "svd_warp.cuh"
@@ -52,31 +58,12 @@ __device__ __forceinline__ unsigned long long update_flops(int m, int n, int Dc,
   return 8ull * m * Dc * n + 32ull * m * n + 4ull * (14ull * a * b * b + 8ull * b * b * b) + 8ull * m * n * k;
 }
 
-__device__ __forceinline__ const GateEntry& gate_at(const TrajParams& p, int s, int k, int b) {
-  return p.gates[((size_t)s * p.K + k) * (p.N - 1) + b];
-}
+// Bonds of truncated layer l have parity (l + first_parity) & 1; the record of
+// bond b in layer l of sample s is layer_off[l] + b / 2 within the sample.
+__device__ __forceinline__ int layer_parity(const TrajParams& p, int l) { return (l + p.first_parity) & 1; }
 
-// Truncated layer l (0..2K): parity l&1; slices of its elementary gates k0 <= k1
-// (k0 == k1 unless the layer merges the half steps of slices k0 and k0+1).
-__device__ __forceinline__ void layer_slices(int l, int K, int& k0, int& k1) {
-  if (l & 1) {
-    k0 = k1 = (l - 1) >> 1;
-  } else if (l == 0) {
-    k0 = k1 = 0;
-  } else if (l == 2 * K) {
-    k0 = k1 = K - 1;
-  } else {
-    k0 = (l >> 1) - 1;
-    k1 = k0 + 1;
-  }
-}
-
-// The 4x4 gate of bond b in truncated layer l.
-__device__ __forceinline__ const double2* layer_gate(const TrajParams& p, int s, int l, int b) {
-  int k0, k1;
-  layer_slices(l, p.K, k0, k1);
-  if (k0 == k1) return gate_at(p, s, k0, b).G;
-  return p.merged + (((size_t)s * (p.K - 1) + k0) * (p.N - 1) + b) * 16;
+__device__ __forceinline__ const LayerGate& layer_rec(const TrajParams& p, int s, int l, int b) {
+  return p.lgates[(size_t)s * p.recs_per_sample + p.layer_off[l] + (b >> 1)];
 }
 
 // ---------------------------------------------------------------------------
@@ -333,97 +320,14 @@ __device__ double2 warp_overlap(const TrajParams& p, const Lay& Yt, const unsign
   return E0[0];
 }
 
-// dO/du for the parameters u of one elementary gate (slice k, bond b), given
-// the mixed two-site density rho it sees: tr(P_u Omega) with
-// Omega = V ((Gam^T) o (e^{i tau Lam} V^dag rho V)) V^dag (Daleckii-Krein),
-// accumulated as 2 Re(conj(O) dO) into the trajectory's gradient row.
-__device__ void gate_gradient(const TrajParams& p, const GateEntry& ge, const double2* rho, int k, int b, double2 wO,
-                              double* gsp_row, WarpCtx& w) {
-  const int lane = w.lane;
-  const int N = p.N;
-  double2* T1 = w.small + 16;
-  double2* T2 = w.small + 32;
-  double2* Om = w.small + 48;
-  const int ri = (lane & 15) >> 2, ci = lane & 3;
-  // T1 = V^dag rho
-  if (lane < 16) {
-    double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int l = 0; l < 4; ++l) cfmac(acc, ge.V[l * 4 + ri], rho[l * 4 + ci]);
-    T1[lane] = acc;
-  }
-  __syncwarp();
-  // Omega' = Gam^T o (e^{i tau lam_i} (T1 V))  -> T2
-  if (lane < 16) {
-    double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int l = 0; l < 4; ++l) cfma(acc, T1[ri * 4 + l], ge.V[l * 4 + ci]);
-    acc = cmulc(acc, ge.E[ri]);
-    T2[lane] = cmul(ge.Gam[ci * 4 + ri], acc);
-  }
-  __syncwarp();
-  // T1 = V Omega'
-  if (lane < 16) {
-    double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int l = 0; l < 4; ++l) cfma(acc, ge.V[ri * 4 + l], T2[l * 4 + ci]);
-    T1[lane] = acc;
-  }
-  __syncwarp();
-  // Omega = T1 V^dag
-  if (lane < 16) {
-    double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int l = 0; l < 4; ++l) cfmac(acc, ge.V[ci * 4 + l], T1[ri * 4 + l]);
-    Om[lane] = acc;
-  }
-  __syncwarp();
-  if (lane < 5) {
-    const double wl = (b == 0) ? 1.0 : 0.5;
-    const double wr = (b + 1 == N - 1) ? 1.0 : 0.5;
-    double2 v;
-    int c = -1, site = -1;
-    if (lane == 0) {  // X on the left site
-      v = make_double2(Om[8].x + Om[13].x + Om[2].x + Om[7].x, Om[8].y + Om[13].y + Om[2].y + Om[7].y);
-      v = cscale(v, wl);
-      c = 0;
-      site = b;
-    } else if (lane == 1) {  // Y on the left site: -i Om[2+s][s] + i Om[s][2+s]
-      const double2 d = make_double2(Om[2].x + Om[7].x - Om[8].x - Om[13].x, Om[2].y + Om[7].y - Om[8].y - Om[13].y);
-      v = cscale(make_double2(-d.y, d.x), wl);
-      c = 1;
-      site = b;
-    } else if (lane == 2) {  // X on the right site
-      v = make_double2(Om[4].x + Om[1].x + Om[14].x + Om[11].x, Om[4].y + Om[1].y + Om[14].y + Om[11].y);
-      v = cscale(v, wr);
-      c = 0;
-      site = b + 1;
-    } else if (lane == 3) {  // Y on the right site: -i Om[2s+1][2s] + i Om[2s][2s+1]
-      const double2 d = make_double2(Om[1].x + Om[11].x - Om[4].x - Om[14].x, Om[1].y + Om[11].y - Om[4].y - Om[14].y);
-      v = cscale(make_double2(-d.y, d.x), wr);
-      c = 1;
-      site = b + 1;
-    } else {  // ZZ
-      v = make_double2(Om[0].x - Om[5].x - Om[10].x + Om[15].x, Om[0].y - Om[5].y - Om[10].y + Om[15].y);
-      c = (p.C == 3) ? 2 : -1;
-      site = b;
-    }
-    if (c >= 0 && p.mask[c * N + site]) {
-      // dF contribution 2 Re(conj(O) dO)
-      const double contrib = 2.0 * (wO.x * v.x + wO.y * v.y);
-      gsp_row[((size_t)k * p.C + c) * N + site] += contrib;
-    }
-  }
-  __syncwarp();
-}
-
 // ---------------------------------------------------------------------------
-// Gradient of one layer: environments, mixed two-site densities, and
-// dO/du = tr(P_u Omega) with Omega = V ((Gam^T) o (e^{i tau Lam} V^dag rho V)) V^dag.
+// Gradient of one layer: environments, mixed two-site densities rho, and
+// dO/du = tr(Q_u rho) for every control u of every gate in the layer, added
+// to the trajectory's gradient row as 2 Re(conj(O) dO/du).
 // ---------------------------------------------------------------------------
 __device__ void layer_gradient(const TrajParams& p, const Lay& Y, const unsigned char* cslot, const StateView av,
                                int s, int l, double2 wO, double* gsp_row, WarpCtx& w, int warp) {
-  const int parity = l & 1;
+  const int parity = layer_parity(p, l);
   const int N = p.N, chi = p.chi;
   const size_t cc = (size_t)chi * chi;
   const int* Dc = slot_dims(cslot);
@@ -528,29 +432,19 @@ __device__ void layer_gradient(const TrajParams& p, const Lay& Y, const unsigned
       if (lane < 16) rho[o] = acc;
     }
     __syncwarp();
-    int k0, k1;
-    layer_slices(l, p.K, k0, k1);
-    // the gate applied last in the layer sees rho; an earlier one sees G_last^dag rho G_last
-    gate_gradient(p, gate_at(p, s, k1, b), rho, k1, b, wO, gsp_row, w);
-    if (k0 != k1) {
-      const double2* G2 = gate_at(p, s, k1, b).G;
-      double2* T1 = w.small + 16;
-      const int ri = (lane & 15) >> 2, ci = lane & 3;
-      if (lane < 16) {  // T1 = rho G2
-        double2 acc = make_double2(0.0, 0.0);
+    // dO/du_q = tr(Q_q rho) = sum_ij Q_q[i][j] rho[j][i]: lane q takes control q
+    const LayerGate& lg = layer_rec(p, s, l, b);
+    const int nq = lg.nq;
+    if (lane < nq) {
+      const double2* Q = lg.Q[lane];
+      double2 v = make_double2(0.0, 0.0);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) cfma(acc, rho[ri * 4 + q], G2[q * 4 + ci]);
-        T1[lane] = acc;
-      }
-      __syncwarp();
-      if (lane < 16) {  // rho <- G2^dag T1
-        double2 acc = make_double2(0.0, 0.0);
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) cfmac(acc, G2[q * 4 + ri], T1[q * 4 + ci]);
-        rho[lane] = acc;
-      }
-      __syncwarp();
-      gate_gradient(p, gate_at(p, s, k0, b), rho, k0, b, wO, gsp_row, w);
+        for (int j = 0; j < 4; ++j) cfma(v, Q[i * 4 + j], rho[j * 4 + i]);
+      // explicit fma: this function is inlined into both history modes, which
+      // must round identically
+      gsp_row[lg.slot[lane]] += 2.0 * fma(wO.x, v.x, wO.y * v.y);
     }
     __syncwarp();
   }
@@ -602,7 +496,7 @@ __device__ __forceinline__ long long update_cost(int Dl, int Dr) {
 // computes it.
 __device__ void apply_layer(const TrajParams& p, const Lay& Y, unsigned char* slot, int s, int l, bool adjoint,
                             bool record, bool count, WarpCtx& w, int warp) {
-  const int parity = l & 1;
+  const int parity = layer_parity(p, l);
   const int nb = (p.N - 1 - parity + 1) / 2;
   const int lane = w.lane;
   if (warp == 0) {
@@ -625,7 +519,7 @@ __device__ void apply_layer(const TrajParams& p, const Lay& Y, unsigned char* sl
     j = __shfl_sync(0xffffffffu, j, 0);
     if (j >= nb) break;
     const int b = w.order[j];
-    two_site_update(p, Y, slot, b, layer_gate(p, s, l, b), adjoint, record, count, w);
+    two_site_update(p, Y, slot, b, layer_rec(p, s, l, b).G, adjoint, record, count, w);
   }
   TNRC_TIC(t_b);
   __syncthreads();
@@ -643,7 +537,7 @@ __device__ int run_trajectory(const TrajParams& p, bool packed, unsigned char* b
   const Lay& Y = p.full;
   const int lane = w.lane;
   const size_t sb = (size_t)Y.L.bytes;
-  const int L = 2 * p.K + 1;  // truncated layers
+  const int L = p.n_layers;  // truncated layers
   unsigned char* a_slot = base;
   unsigned char* c_slot = base + sb;
   unsigned char* ckpt = base + 2 * sb;
@@ -731,7 +625,11 @@ __device__ int run_trajectory(const TrajParams& p, bool packed, unsigned char* b
   return 0;
 }
 
-__global__ void __launch_bounds__(kWarps * 32, 1) traj_kernel(TrajParams p) {
+// Compiled twice: kMinBlocks = 1 lets a thread use up to 255 registers (at
+// most 8 warps per SM); kMinBlocks = 2 caps it at 128 so that 16 warps fit an
+// SM, trading a few spilled values for twice the warps to hide FP64 latency.
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kWarps * 32, kMinBlocks) traj_kernel(TrajParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
   __shared__ double s_disc[kWarps];
@@ -806,14 +704,19 @@ extern "C" cudaError_t tnrc_traj_prepare() {
   if (e != cudaSuccess) return e;
   static bool attr_set[64] = {false};
   if (dev >= 0 && dev < 64 && attr_set[dev]) return cudaSuccess;
-  e = cudaFuncSetAttribute(tnrc::traj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  e = cudaFuncSetAttribute(tnrc::traj_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tnrc::traj_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
   if (e == cudaSuccess && dev >= 0 && dev < 64) attr_set[dev] = true;
   return e;
 }
 
 extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, size_t smem, cudaStream_t st) {
   (void)cudaGetLastError();  // report only this launch below
-  tnrc::traj_kernel<<<grid, p->warps * 32, smem, st>>>(*p);
+  if (p->min_blocks == 2)
+    tnrc::traj_kernel<2><<<grid, p->warps * 32, smem, st>>>(*p);
+  else
+    tnrc::traj_kernel<1><<<grid, p->warps * 32, smem, st>>>(*p);
   return cudaGetLastError();
 }
 

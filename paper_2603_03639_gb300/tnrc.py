@@ -36,7 +36,8 @@ class Problem(ctypes.Structure):
                 ("n_samples", ctypes.c_int32), ("n_controls", ctypes.c_int32), ("n_inputs", ctypes.c_int32),
                 ("control_mask", ctypes.POINTER(ctypes.c_uint8)), ("g_fixed", ctypes.POINTER(ctypes.c_double)),
                 ("checkpoint_every", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("crosstalk_terms", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("crosstalk_terms", ctypes.c_int32),
+                ("trotter_order", ctypes.c_int32), ("substeps", ctypes.c_int32)]
 
 
 class MPSDesc(ctypes.Structure):
@@ -133,7 +134,7 @@ def _pack(state):
 
 
 def make_problem(N, K, dt, chi, M, C, P, cutoff=1e-12, mask=None, g_fixed=None, checkpoint_every=0, warps=0,
-                 ctas_per_sm=0, crosstalk=1):
+                 ctas_per_sm=0, crosstalk=1, order=2, substeps=1):
     """A ``Problem`` plus the arrays it points to (keep both alive)."""
     keep = []
     pb = Problem()
@@ -152,6 +153,8 @@ def make_problem(N, K, dt, chi, M, C, P, cutoff=1e-12, mask=None, g_fixed=None, 
     pb.warps_per_cta = warps
     pb.ctas_per_sm = ctas_per_sm
     pb.crosstalk_terms = crosstalk
+    pb.trotter_order = order
+    pb.substeps = substeps
     return pb, keep
 
 
@@ -166,14 +169,15 @@ def _descs(states):
 
 
 def fidelity_static(N, K, dt, chi, C, inputs, targets, u, J, cutoff=1e-12, mask=None, g_fixed=None,
-                    stream=None, per_traj=False, crosstalk=1):
+                    stream=None, per_traj=False, crosstalk=1, order=2, substeps=1):
     """F (and per-trajectory |O|^2) through tnrc_fidelity_static, which
     allocates no device memory: for callers that cannot call cudaMalloc.
     Calls must not overlap on the GPU (they share one static array)."""
     J = np.ascontiguousarray(J, dtype=np.float64)
     u = np.ascontiguousarray(u, dtype=np.float64)
     M, P = J.shape[0], len(inputs)
-    pb, keep = make_problem(N, K, dt, chi, M, C, P, cutoff, mask, g_fixed, crosstalk=crosstalk)
+    pb, keep = make_problem(N, K, dt, chi, M, C, P, cutoff, mask, g_fixed, crosstalk=crosstalk, order=order,
+                            substeps=substeps)
     ins, kin = _descs(inputs)
     tgs, ktg = _descs(targets)
     F = np.zeros(1)
@@ -201,7 +205,8 @@ class Context:
 
     def __init__(self, N: int, K: int, dt: float, chi: int, M: int, C: int, inputs: Sequence, targets: Sequence,
                  cutoff: float = 1e-12, mask=None, g_fixed=None, checkpoint_every: int = 0,
-                 stream: Optional[int] = None, warps: int = 0, ctas_per_sm: int = 0, crosstalk: int = 1):
+                 stream: Optional[int] = None, warps: int = 0, ctas_per_sm: int = 0, crosstalk: int = 1,
+                 order: int = 2, substeps: int = 1):
         L = lib()
         self.N, self.K, self.C, self.M, self.P = N, K, C, M, len(inputs)
         self.stream = int(stream or 0)
@@ -209,7 +214,7 @@ class Context:
         if len(targets) != self.P:
             raise ValueError("inputs and targets differ in length")
         pb, keep = make_problem(N, K, dt, chi, M, C, self.P, cutoff, mask, g_fixed, checkpoint_every, warps,
-                                ctas_per_sm, crosstalk)
+                                ctas_per_sm, crosstalk, order, substeps)
         packs = [_pack(s) for s in list(inputs) + list(targets)]
         descs = (MPSDesc * len(packs))()
         for d, (dims, data) in zip(descs, packs):

@@ -89,6 +89,48 @@ def test_hard_truncation_chi_4():
     assert grad_close(g, go)
 
 
+@pytest.mark.parametrize("shape", [(8, 1), (4, 2), (2, 4), (8, 2), (4, 4)])
+def test_launch_shapes_and_register_builds(shape):
+    """Every launch shape -- including more than 8 warps per SM, which runs the
+    128-register build of the trajectory kernel -- meets the oracle bars, on a
+    case with small thetas (shared slabs) and one with 64 x 64 thetas (global
+    scratch)."""
+    warps, ctas = shape
+    for w in (synth.WORKLOADS["x8"].replace(M=4),
+              synth.WORKLOADS["ghz30"].replace(N=12, K=5, chi=32, M=1, P=1, u_sigma=1.5, dt=0.25)):
+        u, mask, J, ins, tgs = case(w)
+        pb = oracle_problem(w, u, mask, J, ins, tgs)
+        ctx = gpu_context(w, ins, tgs, mask, warps=warps, ctas_per_sm=ctas)
+        ctx.set_controls(u)
+        ctx.set_noise(J)
+        F, g = ctx.fidelity_grad()
+        Fo, go, Oo = robust.ensemble(pb, want_grad=True)
+        assert abs(F - Fo) <= TOL_F
+        assert np.max(np.abs(ctx.overlaps() - Oo)) <= TOL_O
+        assert grad_close(g, go)
+
+
+@pytest.mark.parametrize("name,order,substeps,N,P", [("cnot50", 1, 1, 8, 2), ("ghz30", 1, 2, 7, 1),
+                                                      ("cnot50", 2, 3, 8, 2), ("x8", 1, 1, 2, 2),
+                                                      ("x8", 1, 3, 5, 2), ("x8", 2, 2, 6, 2)])
+def test_trotter_order_and_substeps(name, order, substeps, N, P):
+    """The first-order slice of Eq. circuit (rotations folded into the bond
+    gates) and several Trotter steps per control bin, against the oracle."""
+    w = synth.WORKLOADS[name].replace(N=N, K=4, chi=16, M=2, P=P, order=order, substeps=substeps)
+    _, (F, g, O), (Fo, go, Oo) = run_both(w)
+    assert abs(F - Fo) <= TOL_F
+    assert np.max(np.abs(O - Oo)) <= TOL_O
+    assert grad_close(g, go)
+
+
+def test_first_order_heisenberg_crosstalk_truncated():
+    w = synth.WORKLOADS["ghz30"].replace(N=10, K=5, chi=8, M=2, P=1, u_sigma=1.0, dt=0.2, order=1, substeps=2,
+                                         crosstalk=3)
+    _, (F, g, O), (Fo, go, Oo) = run_both(w)
+    assert abs(F - Fo) <= TOL_F
+    assert grad_close(g, go)
+
+
 def test_checkpoint_segments_do_not_change_results(monkeypatch):
     """Checkpoint/recompute segmentations (history cap 0 forces that path) and
     the packed history give bitwise the same result."""
