@@ -115,6 +115,48 @@ def trajectory(pb: "_r.Problem", s, p, want_grad=True):
     return O, dO
 
 
+def evolve(pb: "_r.Problem", s, a):
+    """The time-ordered gate sequence of noise sample s applied to the dense
+    vector a without truncation: the elementary layers A(dts/2) B(dts)
+    A(dts/2) of every Trotter step (second order), or Eq. circuit applied
+    literally (first order)."""
+    N = pb.N
+    if pb.order == 1:
+        dts = pb.dt / pb.substeps
+        for k in range(pb.K):
+            for _ in range(pb.substeps):
+                for b in list(range(1, N - 1, 2)) + list(range(0, N - 1, 2)):
+                    xl, yl, xr, yr, c, jx, jy = _r.bond_params(pb, s, k, b)
+                    h = c * np.kron(_g.Z, _g.Z) + jx * np.kron(_g.X, _g.X) + jy * np.kron(_g.Y, _g.Y)
+                    a = apply_two_site(a, _g.expm_hermitian(h, dts)[0], b, N)
+                for cidx, P in ((1, _g.Y), (0, _g.X)):
+                    for j in range(N):
+                        amp = pb.u[k, cidx, j] * pb.mask[cidx, j]
+                        a = apply_one_site(a, np.cos(dts * amp) * _g.I2 - 1j * np.sin(dts * amp) * P, j, N)
+        return a
+    for (k, par, tau) in _r.layers(pb.K, pb.dt, pb.substeps):
+        for b in range(par, N - 1, 2):
+            a = apply_two_site(a, _r.bond_gate(pb, s, k, b, tau)[0], b, N)
+    return a
+
+
+def unitary(pb: "_r.Problem", s):
+    """The 2^N x 2^N propagator of noise sample s, column by column."""
+    n = 2 ** pb.N
+    U = np.zeros((n, n), dtype=np.complex128)
+    for j in range(n):
+        e = np.zeros(n, dtype=np.complex128)
+        e[j] = 1.0
+        U[:, j] = evolve(pb, s, e)
+    return U
+
+
+def gate_overlap(pb: "_r.Problem", s, U_T):
+    """tr(U_T^dag U^(s)) / 2^N, the quantity whose squared modulus is one minus
+    the gate infidelity of Eq. gateinfid."""
+    return np.trace(U_T.conj().T @ unitary(pb, s)) / 2 ** pb.N
+
+
 def full_hamiltonian(pb: "_r.Problem", s, k):
     """H_k of Eq. sysH (ZZ crosstalk) as a dense 2^N x 2^N matrix."""
     N = pb.N

@@ -27,6 +27,15 @@ step (2S layers).
 Objective.  O_sp = <t_p | a_sp(T)>, F = (1/(M P)) sum_sp |O_sp|^2, the
 fidelity whose complement is the ensemble-averaged state infidelity of Sec. II.
 
+Operator form (Sec. II: the propagator itself as an MPO, starting from the
+identity, compressed by the same truncated SVD; Eq. gateinfid).  An operator
+A on N qubits is the vector with site index s = 2 out + in (physical
+dimension 4), scaled so that <<A|B>> = tr(A^dag B) / 2^N; a gate G acts on
+the out indices only, G (x) I_in, and the same algebra then gives
+O = tr(U_T^dag U) / 2^N and F = |O|^2 averaged over the ensemble -- one minus
+the gate infidelity of Eq. gateinfid -- and its gradient, with every 4x4
+gate or Q embedded as G (x) I on the two sites' (out, in) pairs.
+
 Gradient.  With truncated layers l = 1..L, a_l the truncated state after layer
 l and b_l = L_{l+1}^dag ... L_L^dag t (the costate, truncated by the same rule),
 O = <b_l | L_l | a_{l-1}> for every l (App. A), so for a parameter u inside the
@@ -60,6 +69,7 @@ class Problem:
     eps: float = 1e-12
     order: int = 2                # Trotter order: 2 (A B A) or 1 (Eq. circuit)
     substeps: int = 1             # Trotter steps per control bin
+    operator: bool = False        # inputs/targets are operators as vectors (d = 4)
 
     @property
     def M(self):
@@ -201,6 +211,13 @@ def factor_params(pb: Problem, b, kind, k):
     return [((k, c, i), factor_generator(kind))] if pb.mask[c, i] else []
 
 
+def embed_out(G):
+    """G (x) I_in for a 4x4 two-qubit matrix G: the 16x16 matrix on two
+    operator sites with index s = 2 out + in."""
+    E = np.einsum("acbd,ik,jl->aicjbkdl", G.reshape(2, 2, 2, 2), np.eye(2), np.eye(2))
+    return E.reshape(16, 16)
+
+
 def _layer_bonds(N, parity):
     return list(range(parity, N - 1, 2))
 
@@ -221,6 +238,8 @@ def trajectory(pb: Problem, s: int, p: int, want_grad: bool = True, stats=None):
             Mg = np.eye(4, dtype=np.complex128)
             for part in parts:
                 Mg = part[3] @ Mg
+            if pb.operator:
+                Mg = embed_out(Mg)
             gl[b] = (Mg, parts)
             w, kk = _m.two_site_update(B, lam, b, Mg, pb.chi, pb.eps)
             if stats is not None:
@@ -244,11 +263,12 @@ def trajectory(pb: Problem, s: int, p: int, want_grad: bool = True, stats=None):
             # Q_j = (dG_j/du) G_j^dag, L = G_n ... G_{j+1} (the factors after it)
             Lt = np.eye(4, dtype=np.complex128)
             for (kind, k, tau, G, ev, V) in reversed(parts):
-                r = Lt.conj().T @ rho @ Lt
+                Le = embed_out(Lt) if pb.operator else Lt
+                r = Le.conj().T @ rho @ Le
                 for idx, gen in factor_params(pb, b, kind, k):
                     dG = _g.dexpm_hermitian(ev, V, tau, gen)
                     Q = dG @ G.conj().T
-                    dO[idx] += np.trace(Q @ r)
+                    dO[idx] += np.trace((embed_out(Q) if pb.operator else Q) @ r)
                 Lt = Lt @ G
         for b in _layer_bonds(N, par):
             Mg = gate_cache[li][b][0]
@@ -280,7 +300,8 @@ def from_workload(prob: dict, J: np.ndarray, g_fixed=None) -> Problem:
     return Problem(N=w.N, K=w.K, dt=w.dt, C=w.C, chi=w.chi, u=prob["u"], mask=prob["mask"],
                    J=J, inputs=[m.sites for m in prob["inputs"]],
                    targets=[m.sites for m in prob["targets"]], g_fixed=g_fixed,
-                   eps=w.sv_cutoff, order=getattr(w, "order", 2), substeps=getattr(w, "substeps", 1))
+                   eps=w.sv_cutoff, order=getattr(w, "order", 2), substeps=getattr(w, "substeps", 1),
+                   operator=getattr(w, "operator", False))
 
 
 def per_gate_infidelity(chi_bar: float, n: int, qubits_per_gate: int) -> float:

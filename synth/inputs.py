@@ -24,13 +24,16 @@ import numpy as np
 __all__ = [
     "MPS", "Workload", "WORKLOADS", "controls", "pi_pulse_controls",
     "product_inputs", "zero_state", "x_targets", "cnot_targets", "ghz_mps",
-    "heisenberg_ground_mps", "control_mask", "make_problem",
+    "heisenberg_ground_mps", "control_mask", "make_problem", "identity_operator", "x_gate_operator",
+    "cnot_gate_operator",
 ]
 
 
 @dataclasses.dataclass
 class MPS:
-    """A matrix-product state: ``sites[i]`` has shape (D_{i-1}, 2, D_i)."""
+    """A matrix-product state: ``sites[i]`` has shape (D_{i-1}, d, D_i), d = 2
+    for qubit states, d = 4 for operators written as vectors (site index
+    s = 2 out + in)."""
 
     sites: List[np.ndarray]
 
@@ -46,20 +49,20 @@ class MPS:
 
     def pack(self):
         """(bond_dims int32 [N+1], data complex128 flat, site-major, each site
-        (D_l, 2, D_r) row-major) -- the layout the C ABI takes."""
+        (D_l, d, D_r) row-major) -- the layout the C ABI takes."""
         data = np.concatenate([np.ascontiguousarray(s, dtype=np.complex128).ravel()
                                for s in self.sites])
         return self.bond_dims, data
 
     @staticmethod
-    def unpack(bond_dims, data) -> "MPS":
+    def unpack(bond_dims, data, d=2) -> "MPS":
         bond_dims = np.asarray(bond_dims, dtype=np.int64)
         data = np.asarray(data, dtype=np.complex128)
         sites, off = [], 0
         for i in range(len(bond_dims) - 1):
             dl, dr = int(bond_dims[i]), int(bond_dims[i + 1])
-            sites.append(data[off:off + dl * 2 * dr].reshape(dl, 2, dr).copy())
-            off += dl * 2 * dr
+            sites.append(data[off:off + dl * d * dr].reshape(dl, d, dr).copy())
+            off += dl * d * dr
         return MPS(sites)
 
     def copy(self) -> "MPS":
@@ -183,6 +186,48 @@ def ghz_mps(N: int) -> MPS:
     return MPS([first] + [mid.copy() for _ in range(N - 2)] + [last])
 
 
+# --------------------------------------------------------------------------
+# operators as vectors (d = 4, site index s = 2 out + in), normalised so that
+# <<A|B>> = tr(A^dag B) / 2^N
+# --------------------------------------------------------------------------
+
+def _vec(op2):
+    return np.asarray(op2, dtype=np.complex128).reshape(4)
+
+
+def identity_operator(N: int) -> MPS:
+    """The identity on N qubits: the initial operator U(0) of the MPO evolution."""
+    v = _vec(np.eye(2)) / np.sqrt(2.0)
+    return MPS([v.reshape(1, 4, 1).copy() for _ in range(N)])
+
+
+def x_gate_operator(N: int) -> MPS:
+    """X on every qubit (the parallel-X gate target)."""
+    v = _vec([[0, 1], [1, 0]]) / np.sqrt(2.0)
+    return MPS([v.reshape(1, 4, 1).copy() for _ in range(N)])
+
+
+def cnot_gate_operator(N: int) -> MPS:
+    """CNOT on every pair (2i, 2i+1), control 2i: |0><0| (x) I + |1><1| (x) X,
+    operator bond dimension 2 inside a pair."""
+    if N % 2:
+        raise ValueError("parallel CNOT needs an even chain")
+    P0 = _vec([[1, 0], [0, 0]])
+    P1 = _vec([[0, 0], [0, 1]])
+    I2 = _vec(np.eye(2))
+    X2 = _vec([[0, 1], [1, 0]])
+    sites = []
+    for _ in range(N // 2):
+        a = np.zeros((1, 4, 2), dtype=np.complex128)
+        a[0, :, 0] = P0 / np.sqrt(2.0)
+        a[0, :, 1] = P1 / np.sqrt(2.0)
+        b = np.zeros((2, 4, 1), dtype=np.complex128)
+        b[0, :, 0] = I2 / np.sqrt(2.0)
+        b[1, :, 0] = X2 / np.sqrt(2.0)
+        sites += [a, b]
+    return MPS(sites)
+
+
 def heisenberg_ground_mps(N: int, d_max: int, tol: float = 1e-12):
     """Ground state of H_T = sum_j (XX + YY + ZZ)_{j,j+1} (open chain, Sec. IV)
     by Lanczos (scipy ``eigsh``), then cut into an MPS by successive SVDs
@@ -265,6 +310,8 @@ class Workload:
     crosstalk: int = 1       # 1: ZZ (J^z); 3: J^x XX + J^y YY + J^z ZZ (Eq. Hp)
     order: int = 2           # Trotter order: 2 (A B A) or 1 (the slice of Eq. circuit)
     substeps: int = 1        # Trotter steps per control bin
+    operator: bool = False   # evolve the operator U (MPO, d = 4) from the identity;
+                             # F = |tr(U_T^dag U) / 2^N|^2 (Eq. gateinfid)
 
     @property
     def trajectories(self) -> int:
@@ -283,6 +330,12 @@ class Workload:
 
     def states(self):
         """(inputs[P], targets[P]) as MPS lists."""
+        if self.operator:
+            if self.target == "x":
+                return [identity_operator(self.N)] * self.P, [x_gate_operator(self.N)] * self.P
+            if self.target == "cnot":
+                return [identity_operator(self.N)] * self.P, [cnot_gate_operator(self.N)] * self.P
+            raise ValueError("operator targets: x or cnot")
         if self.target == "x":
             ins = product_inputs(self.N, self.P, self.seed_in)
             return ins, x_targets(ins)
@@ -315,6 +368,10 @@ WORKLOADS = {
     "ghz30": Workload("ghz30", N=30, chi=64, K=200, dt=0.05, C=3, M=512, P=1,
                       noise_dist=0, noise_scale=0.1, seed_u=31, seed_J=32, seed_in=33,
                       target="ghz", g_bonds="all"),
+    # the gate objective of Eq. gateinfid with the MPO of Sec. II (D_max = 20)
+    "cnotgate50": Workload("cnotgate50", N=50, chi=20, K=100, dt=0.05, C=3, M=256, P=1,
+                           noise_dist=1, noise_scale=0.05, seed_u=41, seed_J=42, seed_in=43,
+                           target="cnot", g_bonds="pairs", operator=True),
 }
 
 

@@ -13,7 +13,8 @@ TOL_O = 1e-10          # per-trajectory overlap
 def oracle_problem(w, u, mask, J, inputs, targets, g_fixed=None):
     return robust.Problem(N=w.N, K=w.K, dt=w.dt, C=w.C, chi=w.chi, u=u, mask=mask, J=J,
                           inputs=[m.sites for m in inputs], targets=[m.sites for m in targets],
-                          g_fixed=g_fixed, eps=w.sv_cutoff, order=w.order, substeps=w.substeps)
+                          g_fixed=g_fixed, eps=w.sv_cutoff, order=w.order, substeps=w.substeps,
+                          operator=w.operator)
 
 
 def gpu_context(w, inputs, targets, mask, g_fixed=None, checkpoint_every=0, warps=0, ctas_per_sm=0):

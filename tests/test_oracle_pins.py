@@ -18,11 +18,12 @@ PY = np.array([[0, -1j], [1j, 0]])
 PZ = np.diag([1.0, -1.0]).astype(complex)
 
 
-def mkpb(N, K, dt, C, chi, u, mask, J, inputs, targets, g_fixed=None, eps=1e-12, order=2, substeps=1):
+def mkpb(N, K, dt, C, chi, u, mask, J, inputs, targets, g_fixed=None, eps=1e-12, order=2, substeps=1,
+         operator=False):
     return robust.Problem(N=N, K=K, dt=dt, C=C, chi=chi, u=u, mask=mask,
                           J=np.atleast_2d(J) if np.ndim(J) < 3 else J,
                           inputs=[m.sites for m in inputs], targets=[m.sites for m in targets],
-                          g_fixed=g_fixed, eps=eps, order=order, substeps=substeps)
+                          g_fixed=g_fixed, eps=eps, order=order, substeps=substeps, operator=operator)
 
 
 def rand_products(N, P, seed):
@@ -474,6 +475,122 @@ def test_first_order_schedule_folds_each_site_once():
                 t += 1
         for j in range(N):
             assert seen[j] == ["y", "x"], (N, j, seen[j])
+
+
+# ------------------------------------------ operator (MPO) form, Eq. gateinfid
+def _dense_cnot_pairs(N):
+    c = np.zeros((4, 4), dtype=complex)
+    c[0, 0] = c[1, 1] = c[2, 3] = c[3, 2] = 1.0
+    U = np.ones((1, 1), dtype=complex)
+    for _ in range(N // 2):
+        U = np.kron(U, c)
+    return U
+
+
+def test_operator_vectors_are_the_dense_operators():
+    """<<A|B>> = tr(A^dag B) / 2^N for the identity, parallel X and parallel CNOT."""
+    N = 4
+    dense_ops = {"I": np.eye(16), "X": np.kron(np.kron(PX, PX), np.kron(PX, PX)), "C": _dense_cnot_pairs(N)}
+    mps_ops = {"I": synth.identity_operator(N), "X": synth.x_gate_operator(N), "C": synth.cnot_gate_operator(N)}
+    for a in dense_ops:
+        for b in dense_ops:
+            ref = np.trace(dense_ops[a].conj().T @ dense_ops[b]) / 2 ** N
+            assert abs(mps.overlap(mps_ops[a].sites, mps_ops[b].sites) - ref) < 1e-14
+
+
+def test_operator_pi_pulse_is_the_parallel_x_gate():
+    N, K, dt = 5, 6, 0.1
+    u = synth.pi_pulse_controls(K, 2, N, dt)
+    pb = mkpb(N, K, dt, 2, 8, u, synth.control_mask(2, N), np.zeros(N - 1), [synth.identity_operator(N)],
+              [synth.x_gate_operator(N)], operator=True)
+    F, g, _ = robust.ensemble(pb)
+    assert abs(F - 1.0) < 1e-13 and np.max(np.abs(g)) < 1e-12
+
+
+def test_operator_zero_crosstalk_closed_form():
+    """No interaction: U = (x) u_j with u_j the product of each slice's
+    exp(-i dt (x X + y Y)), so tr(X^{(x)N} U) / 2^N = prod_j tr(X u_j) / 2 --
+    fidelity and every derivative in closed form."""
+    N, K, dt = 4, 5, 0.12
+    rng = np.random.default_rng(81)
+    u = rng.normal(0, 0.8, size=(K, 2, N))
+    pb = mkpb(N, K, dt, 2, 8, u, synth.control_mask(2, N), np.zeros(N - 1), [synth.identity_operator(N)],
+              [synth.x_gate_operator(N)], operator=True)
+    F, g, _ = robust.ensemble(pb)
+    Os, dOs = [], []
+    for i in range(N):
+        U = I2.astype(complex)
+        for k in range(K):
+            U = _rot(u[k, 0, i], u[k, 1, i], dt) @ U
+        Os.append(np.trace(PX @ U) / 2)
+        dd = np.zeros((K, 2), dtype=complex)
+        for k in range(K):
+            for c, wrt in ((0, "x"), (1, "y")):
+                M = I2.astype(complex)
+                for kk in range(K):
+                    M = (_drot(u[kk, 0, i], u[kk, 1, i], dt, wrt) if kk == k else
+                         _rot(u[kk, 0, i], u[kk, 1, i], dt)) @ M
+                dd[k, c] = np.trace(PX @ M) / 2
+        dOs.append(dd)
+    O = np.prod(Os)
+    assert abs(F - abs(O) ** 2) < 1e-13
+    gref = np.zeros((K, 2, N))
+    for i in range(N):
+        rest = np.prod([Os[j] for j in range(N) if j != i])
+        gref[:, :, i] = 2 * np.real(np.conj(O) * rest * dOs[i])
+    assert np.max(np.abs(g - gref)) < 1e-12 * max(1.0, np.max(np.abs(gref)))
+
+
+@pytest.mark.parametrize("order,terms,target", [(2, 1, "cnot"), (2, 3, "x"), (1, 1, "cnot"), (1, 3, "x")])
+def test_operator_mpo_equals_dense_unitary_and_fd(order, terms, target):
+    """The MPO path (untruncated) against the dense propagator built column by
+    column from the same gate sequence: O = tr(U_T^dag U) / 2^N to 1e-12, and
+    the costate gradient against central differences of the dense O."""
+    N, K, dt = 4, 3, 0.2
+    rng = np.random.default_rng(91 + order + terms)
+    u = rng.normal(0, 0.7, size=(K, 3, N))
+    mask = synth.control_mask(3, N, "all")
+    J = noise.sample_J(4, 2, N, 0, 0.3, terms=terms)
+    tg = synth.cnot_gate_operator(N) if target == "cnot" else synth.x_gate_operator(N)
+    UT = _dense_cnot_pairs(N) if target == "cnot" else np.kron(np.kron(PX, PX), np.kron(PX, PX))
+
+    def pbu(uu):
+        return mkpb(N, K, dt, 3, 64, uu, mask, J, [synth.identity_operator(N)], [tg], order=order,
+                    operator=True)
+
+    pb = pbu(u)
+    for s in range(2):
+        o, dO = robust.trajectory(pb, s, 0)
+        assert abs(o - dense.gate_overlap(pb, s, UT)) < 1e-12
+        h = 1e-6
+        for _ in range(6):
+            idx = tuple(int(rng.integers(0, n)) for n in u.shape)
+            if not mask[idx[1], idx[2]]:
+                continue
+            up, um = u.copy(), u.copy()
+            up[idx] += h
+            um[idx] -= h
+            fd = (dense.gate_overlap(pbu(up), s, UT) - dense.gate_overlap(pbu(um), s, UT)) / (2 * h)
+            assert abs(fd - dO[idx]) < 1e-7 * max(1.0, np.max(np.abs(dO)))
+
+
+def test_operator_truncation_converges_in_chi():
+    """The truncated MPO fidelity approaches the exact (dense) gate fidelity
+    as chi grows, and equals it once chi reaches the exact operator rank."""
+    N, K, dt = 6, 4, 0.25
+    rng = np.random.default_rng(97)
+    u = rng.normal(0, 1.2, size=(K, 3, N))
+    mask = synth.control_mask(3, N, "all")
+    J = noise.sample_J(6, 1, N, 0, 0.2)
+    UT = _dense_cnot_pairs(N)
+    errs = []
+    for chi in (2, 4, 8, 64):
+        pb = mkpb(N, K, dt, 3, chi, u, mask, J, [synth.identity_operator(N)], [synth.cnot_gate_operator(N)],
+                  operator=True)
+        o, _ = robust.trajectory(pb, 0, 0, want_grad=False)
+        errs.append(abs(abs(o) ** 2 - abs(dense.gate_overlap(pb, 0, UT)) ** 2))
+    assert errs[-1] < 1e-12
+    assert errs[2] <= errs[0] + 1e-12
 
 
 # ----------------------------------------------------------------- invariants
