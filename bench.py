@@ -45,15 +45,25 @@ def fp64_peak_tflops():
     return 2.0 * FP64_FMA_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
 
 
+def form_kwargs(w):
+    """Context keyword arguments for the workload's time discretisation and form."""
+    return {"crosstalk": w.crosstalk, "order": w.order, "substeps": w.substeps, "operator": w.operator}
+
+
 def workload_config(w):
-    return {"workload": "%s: %s on N=%d, chi_max=%d, K=%d, dt=%g, C=%d, M=%d, P=%d, %s J, controls N(0,%g^2)"
-                        % (w.name, {"x": "parallel X", "cnot": "parallel CNOT", "ghz": "GHZ preparation",
-                                    "heisenberg": "Heisenberg ground state"}[w.target],
-                           w.N, w.chi, w.K, w.dt, w.C, w.M, w.P,
-                           ("U[-%g,%g]" % (w.noise_scale, w.noise_scale)) if w.noise_dist == 0
-                           else ("N(0,%g^2)" % w.noise_scale), w.u_sigma),
-            "N": w.N, "chi_max": w.chi, "K": w.K, "M": w.M, "P": w.P, "C": w.C, "dt": w.dt,
-            "slice_steps_per_eval": w.slice_steps}
+    kind = {"x": "parallel X", "cnot": "parallel CNOT", "ghz": "GHZ preparation",
+            "heisenberg": "Heisenberg ground state"}[w.target]
+    if w.operator:
+        kind += " gate (MPO from the identity, |tr(U_T^dag U)/2^N|^2)"
+    cfg = {"workload": "%s: %s on N=%d, chi_max=%d, K=%d, dt=%g, C=%d, M=%d, P=%d, %s J, controls N(0,%g^2)"
+                       % (w.name, kind, w.N, w.chi, w.K, w.dt, w.C, w.M, w.P,
+                          ("U[-%g,%g]" % (w.noise_scale, w.noise_scale)) if w.noise_dist == 0
+                          else ("N(0,%g^2)" % w.noise_scale), w.u_sigma),
+           "N": w.N, "chi_max": w.chi, "K": w.K, "M": w.M, "P": w.P, "C": w.C, "dt": w.dt,
+           "slice_steps_per_eval": w.slice_steps}
+    if w.order != 2 or w.substeps != 1 or w.crosstalk != 1 or w.operator:
+        cfg.update(trotter_order=w.order, substeps=w.substeps, crosstalk_terms=w.crosstalk, operator=w.operator)
+    return cfg
 
 
 class ClockSampler:
@@ -124,7 +134,7 @@ def oracle_sample(w, n_traj, K_s, workers):
     from oracle import noise, robust, runner
     ws = w.replace(K=K_s)
     prob = synth.make_problem(ws)
-    J = noise.sample_J(w.seed_J, n_traj, w.N, w.noise_dist, w.noise_scale)
+    J = noise.sample_J(w.seed_J, n_traj, w.N, w.noise_dist, w.noise_scale, terms=w.crosstalk)
     pb = robust.from_workload(prob, J)
     pairs = [(s, 0) for s in range(n_traj)]
     _, secs, used = runner.run(pb, pairs, want_grad=True, workers=workers)
@@ -216,7 +226,7 @@ def gpu_arm(args, w):
     from paper_2603_03639_gb300 import autotune
     tuned = autotune.lookup(w.N, w.K, w.chi, w.M, w.P, w.C, grad=True)
     ctx = Context(w.N, w.K, w.dt, w.chi, w.M, w.C, ins, tgs, cutoff=w.sv_cutoff, mask=mask,
-                  stream=stream.cuda_stream, warps=tuned[0], ctas_per_sm=tuned[1])
+                  stream=stream.cuda_stream, warps=tuned[0], ctas_per_sm=tuned[1], **form_kwargs(w))
     u_dev = torch.tensor(u, dtype=torch.float64, device=dev)
     F_dev = torch.zeros(1, dtype=torch.float64, device=dev)
     g_dev = torch.zeros(u.shape, dtype=torch.float64, device=dev)
@@ -226,7 +236,7 @@ def gpu_arm(args, w):
     def step_seed(i):
         # step i draws a fresh global ensemble of world*M samples; this rank
         # evaluates its slice of it
-        return shard_seed(w.seed_J + 7919 * i, rank, w.M, w.N, w.noise_dist)
+        return shard_seed(w.seed_J + 7919 * i, rank, w.M, w.N, w.noise_dist, terms=w.crosstalk)
 
     def step(i):
         ctx.set_controls_dev(u_dev.data_ptr())
@@ -450,7 +460,7 @@ def plain_arm(args, w):
             os.environ["TNRC_GRID"] = "1"
         try:
             ctx = Context(ws.N, ws.K, ws.dt, ws.chi, ws.M, ws.C, ins, tgs, cutoff=ws.sv_cutoff, mask=ws.mask(),
-                          warps=tuned[0], ctas_per_sm=tuned[1])
+                          warps=tuned[0], ctas_per_sm=tuned[1], **form_kwargs(ws))
         finally:
             os.environ.pop("TNRC_GRID", None)
         ctx.set_controls(ws.controls())

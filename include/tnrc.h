@@ -39,9 +39,9 @@
  *     k = min(chi_max, #{sigma_i > max(sv_cutoff, 1e-13) sigma_1}) largest
  *     singular values (at least one) and renormalise them to unit norm.
  *   - MPS buffers (tnrc_mps.data): interleaved complex128, site-major, site i
- *     stored as a row-major [D_i][2][D_{i+1}] block; bond_dims has N+1
- *     entries with bond_dims[0] = bond_dims[N] = 1.  States are normalised on
- *     entry.
+ *     stored as a row-major [D_i][d][D_{i+1}] block (d = 2, or 4 with
+ *     operator_form); bond_dims has N+1 entries with bond_dims[0] =
+ *     bond_dims[N] = 1.  States are normalised on entry.
  *   - Ownership: every host pointer passed in is borrowed for the duration of
  *     the call and copied; the context owns all device memory it uses.
  *     Output host buffers are written only when the call returns TNRC_OK.
@@ -76,7 +76,7 @@ typedef struct tnrc_ctx tnrc_ctx;
 typedef struct {
   int32_t n_sites;
   const int32_t* bond_dims; /* [N+1] */
-  const double* data;       /* interleaved complex128, sum_i D_i*2*D_{i+1} values */
+  const double* data;       /* interleaved complex128, sum_i D_i*d*D_{i+1} values */
 } tnrc_mps;
 
 /* The problem statement (Sec. II-IV): chain, time grid, truncation, ensemble. */
@@ -85,7 +85,8 @@ typedef struct {
   int32_t n_sites;               /* N >= 2                                                 */
   int32_t n_slices;              /* K >= 1 piecewise-constant control bins                 */
   double dt;                     /* slice length (> 0)                                     */
-  int32_t chi_max;               /* bond-dimension cap, 1 <= chi_max <= 64                  */
+  int32_t chi_max;               /* bond-dimension cap, 1 <= chi_max <= 64 (<= 32 with
+                                    operator_form)                                          */
   double sv_cutoff;              /* relative singular-value cutoff (>= 0; 1e-12 typical)   */
   int32_t n_samples;             /* M >= 1 noise realisations                              */
   int32_t n_controls;            /* C = 2 (x, y) or 3 (x, y, g)                             */
@@ -103,6 +104,13 @@ typedef struct {
                                     in the order (x, y, z)                                 */
   int32_t trotter_order;         /* 2 (or 0): A(dts/2) B(dts) A(dts/2); 1: Eq. circuit      */
   int32_t substeps;              /* Trotter steps per slice, >= 1 (0 = 1)                   */
+  int32_t operator_form;         /* 0: inputs/targets are states (physical dimension 2);
+                                    1: they are operators written as vectors (MPO of Sec. II,
+                                    physical dimension 4, site index s = 2 out + in, scaled so
+                                    that <<A|B>> = tr(A^dag B) / 2^N); every gate acts as
+                                    G (x) I on the out indices, so with input = the identity
+                                    O = tr(U_T^dag U) / 2^N and F is one minus the gate
+                                    infidelity of Eq. gateinfid                             */
 } tnrc_problem;
 
 /* Per-call statistics of the last tnrc_fidelity / tnrc_fidelity_grad. */

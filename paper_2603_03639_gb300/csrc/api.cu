@@ -34,7 +34,8 @@ constexpr int kMaxInputDim = 128;
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
-// Capacities min(2^i, 2^(N-i), cap), site offsets and byte layout of a slot.
+// Capacities min(d^i, d^(N-i), cap), site offsets and byte layout of a slot
+// (physical dimension d = 2 for states, 4 for operators).
 struct Layout {
   std::vector<int> dcap;      // [N+1] capacity of D[i]
   std::vector<int> site_off;  // [N]
@@ -42,19 +43,20 @@ struct Layout {
   int seg = 1, nseg = 1;
 };
 
-Layout make_layout(int N, int cap) {
+Layout make_layout(int N, int cap, int d) {
   Layout Y;
   Y.dcap.assign(N + 1, 1);
+  const int lg = d == 4 ? 2 : 1;   // log2 d
   for (int i = 1; i < N; ++i) {
-    const int a = i >= 30 ? cap : std::min(1 << i, cap);
-    const int b = (N - i) >= 30 ? cap : std::min(1 << (N - i), cap);
+    const int a = i * lg >= 30 ? cap : std::min(1 << (i * lg), cap);
+    const int b = (N - i) * lg >= 30 ? cap : std::min(1 << ((N - i) * lg), cap);
     Y.dcap[i] = std::min(a, b);
   }
   Y.site_off.resize(N);
   int64_t elems = 0;
   for (int i = 0; i < N; ++i) {
     Y.site_off[i] = (int)elems;
-    elems += (int64_t)Y.dcap[i] * 2 * Y.dcap[i + 1];
+    elems += (int64_t)Y.dcap[i] * d * Y.dcap[i + 1];
     elems = align_up(elems, 2);
   }
   Y.L.N = N;
@@ -68,6 +70,7 @@ Layout make_layout(int N, int cap) {
 struct Plan {
   int N, K, C, chi, M, P, T, terms;
   int order, nsub;            // Trotter order (1 or 2), Trotter steps per control bin
+  int d;                      // physical dimension: 2 (states) or 4 (operators)
   int n_layers, first_parity, recs;   // truncated layers, parity of layer 0, layer-gate records per sample
   std::vector<int> layer_off; // [n_layers + 1] first record of each layer within a sample
   int seg, nseg;
@@ -105,6 +108,9 @@ bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, boo
   P.terms = pb->crosstalk_terms == 3 ? 3 : 1;
   if (pb->trotter_order < 0 || pb->trotter_order > 2 || pb->substeps < 0) return false;
   P.order = pb->trotter_order == 1 ? 1 : 2;
+  if (pb->operator_form != 0 && pb->operator_form != 1) return false;
+  P.d = pb->operator_form ? 4 : 2;
+  if (P.d * chi > tnrc::kMaxDim) return false;   // theta sides d chi must fit the per-warp arrays
   P.nsub = pb->substeps > 0 ? pb->substeps : 1;
   if ((long long)K * P.nsub > (1 << 20)) return false;
   // truncated layers: 2S+1 (second order; A half steps merged at step
@@ -124,7 +130,7 @@ bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, boo
                                    : (int)std::ceil(std::sqrt((double)L));
   P.nseg = (L + P.seg - 1) / P.seg;
   {
-    Layout Y = make_layout(N, chi);
+    Layout Y = make_layout(N, chi, P.d);
     P.dcap = Y.dcap;
     P.site_off = Y.site_off;
     P.L = Y.L;
@@ -142,7 +148,7 @@ bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, boo
   // the register file holds 8 warps of the 255-register build per SM and 16 of
   // the 128-register build; more than 8 warps per SM select the latter
   const int ctas_per_sm =
-      std::max(1, std::min(pb->ctas_per_sm > 0 ? pb->ctas_per_sm : 1, 2 * tnrc::kWarps / P.warps));
+      std::max(1, std::min(pb->ctas_per_sm > 0 ? pb->ctas_per_sm : 1, (P.d == 4 ? 1 : 2) * tnrc::kWarps / P.warps));
   P.min_blocks = (P.warps * ctas_per_sm > tnrc::kWarps) ? 2 : 1;
   // each warp's shared slab holds theta^dagger up to slab_elems complex values
   // (wider thetas use global scratch): split what the resident CTAs of an SM
@@ -151,10 +157,10 @@ bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, boo
     const int per_sm = 220 * 1024 / ctas_per_sm;
     const int small = (int)tnrc_traj_smem(P.warps, 0) + 1024;
     const int per_warp = std::max(0, per_sm - small) / P.warps / 16;
-    P.slab_elems = std::max(256, std::min(4 * chi * chi, per_warp / 32 * 32));
+    P.slab_elems = std::max(256, std::min(P.d * P.d * chi * chi, per_warp / 32 * 32));
   }
   const int64_t cc = (int64_t)chi * chi;
-  P.scratch_elems = 16 * cc;
+  P.scratch_elems = 4 * (int64_t)P.d * P.d * cc;   // Phi and theta (d chi)^2 each, and more
   P.env_elems = 2 * (int64_t)(N + 1) * cc;
   P.work_stride = (int64_t)(2 + P.nseg + P.seg) * P.L.bytes;
   const int64_t per_cta = P.work_stride + (P.scratch_elems * P.warps + P.env_elems) * 16;
@@ -205,7 +211,7 @@ bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, boo
   return true;
 }
 
-bool valid_mps(const tnrc_mps& m, int N) {
+bool valid_mps(const tnrc_mps& m, int N) {  // the data size follows from bond_dims and d
   if (m.n_sites != N || !m.bond_dims || !m.data) return false;
   if (m.bond_dims[0] != 1 || m.bond_dims[N] != 1) return false;
   for (int i = 0; i <= N; ++i)
@@ -290,7 +296,8 @@ tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, dou
   tp.want_grad = grad ? 1 : 0;
   tp.warps = P.warps;
   tp.slab_elems = P.slab_elems;
-  tp.min_blocks = P.min_blocks;
+  tp.min_blocks = P.d == 4 ? 1 : P.min_blocks;
+  tp.phys_dim = P.d;
   tp.full.L = P.L;
   tp.full.site_off = ctx->at<int>(P.off_siteoff);
   tp.full.dcap = ctx->at<int>(P.off_dcap);
@@ -495,18 +502,18 @@ tnrc_status tnrc_create(const tnrc_problem* pb, const tnrc_mps* inputs, const tn
         dims[(size_t)j * (N + 1) + i] = m.bond_dims[i];
         dmax = std::max(dmax, m.bond_dims[i]);
       }
-      for (int i = 0; i < N; ++i) total += (long long)m.bond_dims[i] * 2 * m.bond_dims[i + 1];
+      for (int i = 0; i < N; ++i) total += (long long)m.bond_dims[i] * P.d * m.bond_dims[i + 1];
     }
     std::vector<double> raw((size_t)total * 2);
     for (int j = 0; j < nmps; ++j) {
       const tnrc_mps& m = (j < P.P) ? inputs[j] : targets[j - P.P];
       long long cnt = 0;
-      for (int i = 0; i < N; ++i) cnt += (long long)m.bond_dims[i] * 2 * m.bond_dims[i + 1];
+      for (int i = 0; i < N; ++i) cnt += (long long)m.bond_dims[i] * P.d * m.bond_dims[i + 1];
       for (long long e = 0; e < 2 * cnt; ++e)
         if (!std::isfinite(m.data[e])) return bail(TNRC_E_INVALID);
       std::memcpy(raw.data() + offs[j] * 2, m.data, (size_t)cnt * 16);
     }
-    const long long wstride = (long long)(N + 4) * 2 * dmax * dmax;
+    const long long wstride = (long long)(N + 4) * P.d * dmax * dmax;
     void *d_dims = nullptr, *d_raw = nullptr, *d_offs = nullptr, *d_work = nullptr;
     bool ok = cudaMalloc(&d_dims, dims.size() * 4) == cudaSuccess && cudaMalloc(&d_raw, raw.size() * 8) == cudaSuccess &&
               cudaMalloc(&d_offs, offs.size() * 8) == cudaSuccess &&
@@ -520,6 +527,7 @@ tnrc_status tnrc_create(const tnrc_problem* pb, const tnrc_mps* inputs, const tn
       tnrc::CanonArgs a{};
       a.N = N;
       a.chi = P.chi;
+      a.d = P.d;
       a.eps = ctx->eps;
       a.dmax = dmax;
       a.raw_dims = (const int*)d_dims;

@@ -2,11 +2,11 @@
 // App. A needs the target in the same right-canonical form with Schmidt values
 // that the TEBD update keeps; Sec. IV gives the targets as arbitrary MPS).
 //
-// One warp per MPS:
-//   left sweep : site i as (2 D_i) x D_{i+1}; SVD -> U S W^dag; site i <- U_r
+// One warp per MPS (physical dimension d = 2 for states, 4 for operators):
+//   left sweep : site i as (d D_i) x D_{i+1}; SVD -> U S W^dag; site i <- U_r
 //                (left isometry, numerically-zero values dropped), site i+1 <- (U_r^dag M) site i+1;
 //   right sweep: with everything to the left left-isometric, site i (times the
-//                carry from the right) as D_i x (2 D_{i+1}); SVD -> U S Y^dag;
+//                carry from the right) as D_i x (d D_{i+1}); SVD -> U S Y^dag;
 //                B_i <- Y_k^dag, lam_{i-1} <- S_k/|S_k|, carry <- M Y_k/|S_k| = U_k S_k/|S_k|;
 //   B_0 <- site 0 times the carry, normalised.
 #include "svd_warp.cuh"
@@ -20,8 +20,8 @@ __global__ void canon_kernel(CanonArgs a) {
   __shared__ int D[257];
   const int lane = threadIdx.x;
   const int mi = blockIdx.x;
-  const int N = a.N, dm = a.dmax;
-  const size_t sz = (size_t)2 * dm * dm;
+  const int N = a.N, dm = a.dmax, d = a.d;
+  const size_t sz = (size_t)d * dm * dm;
   double2* W = a.work + (size_t)mi * a.work_stride;   // N sites, each sz
   double2* Mb = W + (size_t)N * sz;
   double2* T = Mb + sz;
@@ -34,7 +34,7 @@ __global__ void canon_kernel(CanonArgs a) {
     const double2* src = a.raw_data + a.raw_off[mi];
     size_t off = 0;
     for (int i = 0; i < N; ++i) {
-      const int cnt = D[i] * 2 * D[i + 1];
+      const int cnt = D[i] * d * D[i + 1];
       for (int e = lane; e < cnt; e += 32) W[(size_t)i * sz + e] = src[off + e];
       off += cnt;
     }
@@ -44,7 +44,7 @@ __global__ void canon_kernel(CanonArgs a) {
   // ---- left sweep ----
   for (int i = 0; i + 1 < N; ++i) {
     const int dl = D[i], dr = D[i + 1], dn = D[i + 2];
-    const int n = 2 * dl, m = dr;
+    const int n = d * dl, m = dr;
     double2* Wi = W + (size_t)i * sz;
     double fro = 0.0;
     for (int e = lane; e < n * m; e += 32) {
@@ -76,20 +76,20 @@ __global__ void canon_kernel(CanonArgs a) {
     __syncwarp();
     // site i+1 <- carry . site i+1
     double2* Wn = W + (size_t)(i + 1) * sz;
-    for (int e = lane; e < r * 2 * dn; e += 32) {
-      const int j = e / (2 * dn), rest = e - j * 2 * dn;
+    for (int e = lane; e < r * d * dn; e += 32) {
+      const int j = e / (d * dn), rest = e - j * d * dn;
       double2 acc = make_double2(0.0, 0.0);
-      for (int be = 0; be < m; ++be) cfma(acc, carry[(size_t)j * m + be], Wn[(size_t)be * 2 * dn + rest]);
+      for (int be = 0; be < m; ++be) cfma(acc, carry[(size_t)j * m + be], Wn[(size_t)be * d * dn + rest]);
       tmp[e] = acc;
     }
     __syncwarp();
-    for (int e = lane; e < r * 2 * dn; e += 32) Wn[e] = tmp[e];
+    for (int e = lane; e < r * d * dn; e += 32) Wn[e] = tmp[e];
     if (lane == 0) D[i + 1] = r;
     __syncwarp();
   }
   {  // normalise the last site
     double2* Wl = W + (size_t)(N - 1) * sz;
-    const int cnt = D[N - 1] * 2;
+    const int cnt = D[N - 1] * d;
     double s = 0.0;
     for (int e = lane; e < cnt; e += 32) s += cabs2(Wl[e]);
     s = warp_sum(s);
@@ -108,14 +108,14 @@ __global__ void canon_kernel(CanonArgs a) {
   for (int i = N - 1; i >= 1; --i) {
     const int dl = D[i], dr = D[i + 1];
     double2* Wi = W + (size_t)i * sz;
-    const int n = 2 * cr, m = dl;
+    const int n = d * cr, m = dl;
     // M[al][s][c] = sum_r Wi[al][s][r] carry[r][c]
     double fro = 0.0;
-    for (int e = lane; e < dl * 2 * cr; e += 32) {
-      const int al = e / (2 * cr), rest = e - al * 2 * cr;
+    for (int e = lane; e < dl * d * cr; e += 32) {
+      const int al = e / (d * cr), rest = e - al * d * cr;
       const int s = rest / cr, c = rest - s * cr;
       double2 acc = make_double2(0.0, 0.0);
-      for (int r = 0; r < dr; ++r) cfma(acc, Wi[(size_t)al * 2 * dr + s * dr + r], carry[(size_t)r * cr + c]);
+      for (int r = 0; r < dr; ++r) cfma(acc, Wi[(size_t)al * d * dr + s * dr + r], carry[(size_t)r * cr + c]);
       Mb[e] = acc;
       T[e] = cconj(acc);  // column al of M^dagger, row (s c)
       fro += cabs2(acc);
@@ -151,7 +151,7 @@ __global__ void canon_kernel(CanonArgs a) {
     double2* W0 = W;
     double2* B0 = sites + a.site_off[0];
     double s = 0.0;
-    for (int e = lane; e < 2 * cr; e += 32) {
+    for (int e = lane; e < d * cr; e += 32) {
       const int sidx = e / cr, c = e - sidx * cr;
       double2 acc = make_double2(0.0, 0.0);
       for (int r = 0; r < dr; ++r) cfma(acc, W0[(size_t)sidx * dr + r], carry[(size_t)r * cr + c]);
@@ -161,7 +161,7 @@ __global__ void canon_kernel(CanonArgs a) {
     s = warp_sum(s);
     const double inv = rsqrt(s);
     __syncwarp();
-    for (int e = lane; e < 2 * cr; e += 32) B0[e] = cscale(tmp[e], inv);
+    for (int e = lane; e < d * cr; e += 32) B0[e] = cscale(tmp[e], inv);
     if (lane == 0) {
       SD[0] = 1;
       SD[N] = 1;

@@ -86,6 +86,10 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   const int terms = pb->crosstalk_terms == 3 ? 3 : 1;
   if (pb->trotter_order < 0 || pb->trotter_order > 2 || pb->substeps < 0) return TNRC_E_INVALID;
   const int order = pb->trotter_order == 1 ? 1 : 2;
+  if (pb->operator_form != 0 && pb->operator_form != 1) return TNRC_E_INVALID;
+  const int d = pb->operator_form ? 4 : 2;   // physical dimension
+  const int lg = pb->operator_form ? 2 : 1;  // log2 d
+  if (d * chi > tnrc::kMaxDim) return TNRC_E_INVALID;
   const int nsub = pb->substeps > 0 ? pb->substeps : 1;
   if ((long long)K * nsub > (1 << 20)) return TNRC_E_INVALID;
   // truncated layers (alternating bond parity) and their gate records per sample
@@ -119,14 +123,14 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   // ---- layout of one state slot (capacity D_i = min(2^i, 2^(N-i), chi)) ----
   std::vector<int> dcap(N + 1, 1), site_off(N);
   for (int i = 1; i < N; ++i) {
-    const int a = i >= 30 ? chi : std::min(1 << i, chi);
-    const int b = (N - i) >= 30 ? chi : std::min(1 << (N - i), chi);
+    const int a = i * lg >= 30 ? chi : std::min(1 << (i * lg), chi);
+    const int b = (N - i) * lg >= 30 ? chi : std::min(1 << ((N - i) * lg), chi);
     dcap[i] = std::min(a, b);
   }
   int64_t elems = 0;
   for (int i = 0; i < N; ++i) {
     site_off[i] = (int)elems;
-    elems += (int64_t)dcap[i] * 2 * dcap[i + 1];
+    elems += (int64_t)dcap[i] * d * dcap[i + 1];
     elems = (elems + 1) / 2 * 2;
   }
   tnrc::SlotLayout L;
@@ -144,9 +148,9 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
     const tnrc_mps& m = (j < P) ? inputs[j] : targets[j - P];
     roffs[j] = rtotal;
     for (int i = 0; i <= N; ++i) rdims[(size_t)j * (N + 1) + i] = m.bond_dims[i];
-    for (int i = 0; i < N; ++i) rtotal += (long long)m.bond_dims[i] * 2 * m.bond_dims[i + 1];
+    for (int i = 0; i < N; ++i) rtotal += (long long)m.bond_dims[i] * d * m.bond_dims[i + 1];
   }
-  const long long cwork = (long long)(N + 4) * 2 * dmax * dmax;
+  const long long cwork = (long long)(N + 4) * d * dmax * dmax;
   int64_t off = 0;
   auto take = [&](int64_t bytes) {
     const int64_t o = off;
@@ -165,9 +169,9 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   int maxb = 0;
   for (int par = 0; par < 2; ++par) maxb = std::max(maxb, (N - 1 - par + 1) / 2);
   const int warps = std::max(2, std::min(tnrc::kWarps, maxb));
-  const int slab = std::min(1024, 4 * chi * chi);
+  const int slab = std::min(1024, d * d * chi * chi);
   const int64_t cc = (int64_t)chi * chi;
-  const int64_t scratch_elems = 16 * cc;
+  const int64_t scratch_elems = 4 * (int64_t)d * d * cc;
   const int64_t env_elems = 2 * (int64_t)(N + 1) * cc;
   const int64_t per_cta = up(L.bytes) + up(warps * scratch_elems * 16) + up(env_elems * 16);
   if (off + per_cta > (int64_t)kStaticBytes) return TNRC_E_TOO_LARGE;
@@ -201,7 +205,7 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   for (int j = 0; j < 2 * P; ++j) {
     const tnrc_mps& m = (j < P) ? inputs[j] : targets[j - P];
     long long cnt = 0;
-    for (int i = 0; i < N; ++i) cnt += (long long)m.bond_dims[i] * 2 * m.bond_dims[i + 1];
+    for (int i = 0; i < N; ++i) cnt += (long long)m.bond_dims[i] * d * m.bond_dims[i + 1];
     for (long long e = 0; e < 2 * cnt; ++e)
       if (!std::isfinite(m.data[e])) return TNRC_E_INVALID;
     std::memcpy(raw.data() + roffs[j] * 2, m.data, (size_t)cnt * 16);
@@ -233,6 +237,7 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   ca.chi = chi;
   ca.eps = eps;
   ca.dmax = dmax;
+  ca.d = d;
   ca.raw_dims = reinterpret_cast<const int*>(base + o_rdims);
   ca.raw_data = reinterpret_cast<const double2*>(base + o_raw);
   ca.raw_off = reinterpret_cast<const long long*>(base + o_roffs);
@@ -265,6 +270,7 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   tp.warps = warps;
   tp.slab_elems = slab;
   tp.min_blocks = 1;
+  tp.phys_dim = d;
   tp.full.L = L;
   tp.full.site_off = reinterpret_cast<const int*>(base + o_site);
   tp.full.dcap = reinterpret_cast<const int*>(base + o_dcap);

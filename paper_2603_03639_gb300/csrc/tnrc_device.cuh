@@ -87,6 +87,7 @@ struct TrajParams {
   double dt, eps;              // eps = max(cutoff, kZeroFloor)
   int want_grad;
   int warps;                   // warps per CTA
+  int phys_dim;                // 2: qubit states; 4: operators as vectors (s = 2 out + in)
   int min_blocks;              // register budget of the launch: 1 = up to 8 warps per SM
                                // (255 registers), 2 = up to 16 warps per SM (128 registers)
   int slab_elems;              // complex elements of each warp's shared slab
@@ -116,6 +117,7 @@ struct TrajParams {
 
 struct CanonArgs {
   int N, chi;
+  int d;                       // physical dimension (2 or 4)
   double eps;
   int dmax;
   const int* raw_dims;         // [nmps][N+1]

@@ -67,25 +67,32 @@ __device__ __forceinline__ const LayerGate& layer_rec(const TrajParams& p, int s
 }
 
 // ---------------------------------------------------------------------------
+// Physical dimension kD: 2 for qubit states; 4 for operators written as
+// vectors (site index s = 2 out + in, the MPO of Sec. II), where the 4x4 gate
+// acts on the two out indices and leaves the in indices alone.  With
+// kI = kD / 2, s = o kI + i.
+// ---------------------------------------------------------------------------
 // Two-site update of bond b: theta = lam_{b-1} G (B_b B_{b+1}), truncated SVD,
 // B_{b+1} <- Y_k^dag, B_b <- Phi Y_k / |S_k|, lam_b <- S_k / |S_k|.
 // The SVD: theta P = Q R by pivoted QR (Q not formed; R has r rows, r the
 // numerical rank), then one-sided Jacobi on the r columns of R^dagger:
 // R^dagger V = Z S, so theta = (Q V) S (P Z)^dagger and Y = P Z.
 // ---------------------------------------------------------------------------
+template <int kD>
 __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char* slot, int b, const double2* G,
                                 bool adjoint, bool record, bool count, WarpCtx& w) {
+  constexpr int kI = kD / 2;
   const int lane = w.lane;
   const int chi = p.chi;
   const int lstride = Y.L.chi;
   int* D = slot_dims(slot);
   const int Dl = D[b], Dc = D[b + 1], Dr = D[b + 2];
-  const int m = 2 * Dl, n = 2 * Dr;
+  const int m = kD * Dl, n = kD * Dr;
   double2* sites = slot_sites(slot, Y.L);
   double* lam = slot_lam(slot, Y.L);
   double2* A = sites + Y.site_off[b];
   double2* Bt = sites + Y.site_off[b + 1];
-  double2* T = (m * n <= p.slab_elems) ? w.slab : (w.scratch + (size_t)4 * chi * chi);
+  double2* T = (m * n <= p.slab_elems) ? w.slab : (w.scratch + (size_t)kD * kD * chi * chi);
   double2* Phi = w.scratch;
 
   double2 g[16];
@@ -99,29 +106,36 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   double fro = 0.0;
   for (int it = lane; it < Dl * Dr; it += 32) {
     const int al = it / Dr, ga = it - al * Dr;
-    double2 acc[4];
+    double2 acc[kD * kD];   // (B_b B_{b+1})[al][s1][s2][ga] at s1 kD + s2
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = make_double2(0.0, 0.0);
-    const double2* a0p = A + (size_t)(al * 2) * Dc;
-    const double2* a1p = a0p + Dc;
+    for (int q = 0; q < kD * kD; ++q) acc[q] = make_double2(0.0, 0.0);
+    const double2* ap = A + (size_t)(al * kD) * Dc;
     for (int be = 0; be < Dc; ++be) {
-      const double2 a0 = a0p[be], a1 = a1p[be];
-      const double2 b0 = Bt[(size_t)(be * 2) * Dr + ga], b1 = Bt[(size_t)(be * 2 + 1) * Dr + ga];
-      cfma(acc[0], a0, b0);
-      cfma(acc[1], a0, b1);
-      cfma(acc[2], a1, b0);
-      cfma(acc[3], a1, b1);
+      double2 av[kD], bv[kD];
+#pragma unroll
+      for (int q = 0; q < kD; ++q) {
+        av[q] = ap[(size_t)q * Dc + be];
+        bv[q] = Bt[(size_t)(be * kD + q) * Dr + ga];
+      }
+#pragma unroll
+      for (int q1 = 0; q1 < kD; ++q1)
+#pragma unroll
+        for (int q2 = 0; q2 < kD; ++q2) cfma(acc[q1 * kD + q2], av[q1], bv[q2]);
     }
     const double ll = (b > 0) ? lam[(size_t)(b - 1) * lstride + al] : 1.0;
 #pragma unroll
-    for (int s1 = 0; s1 < 2; ++s1)
+    for (int s1 = 0; s1 < kD; ++s1)
 #pragma unroll
-      for (int s2 = 0; s2 < 2; ++s2) {
-        const int row = s1 * 2 + s2;
+      for (int s2 = 0; s2 < kD; ++s2) {
+        const int o1 = s1 / kI, i1 = s1 % kI, o2 = s2 / kI, i2 = s2 % kI;
+        const int row = o1 * 2 + o2;
         double2 v = make_double2(0.0, 0.0);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) cfma(v, g[row * 4 + q], acc[q]);
-        const size_t idx = (size_t)(al * 2 + s1) * n + s2 * Dr + ga;
+        for (int p1 = 0; p1 < 2; ++p1)
+#pragma unroll
+          for (int p2 = 0; p2 < 2; ++p2)
+            cfma(v, g[row * 4 + p1 * 2 + p2], acc[(p1 * kI + i1) * kD + p2 * kI + i2]);
+        const size_t idx = (size_t)(al * kD + s1) * n + s2 * Dr + ga;
         Phi[idx] = v;
         const double2 th = cscale(v, ll);
         T[idx] = th;
@@ -216,13 +230,15 @@ __device__ __forceinline__ StateView packed_view(const unsigned char* rec, int N
 }
 
 // Bytes of the packed record of a slot (same value in every thread).
+template <int kD>
 __device__ __forceinline__ size_t packed_bytes(const int* D, int N) {
   size_t e = 0;
-  for (int i = 0; i < N; ++i) e += (size_t)D[i] * 2 * D[i + 1];
+  for (int i = 0; i < N; ++i) e += (size_t)D[i] * kD * D[i + 1];
   return packed_header(N) + e * 16;
 }
 
 // CTA-wide: write the packed record of `slot` to `rec`.
+template <int kD>
 __device__ void pack_state(const TrajParams& p, const Lay& Y, const unsigned char* slot, unsigned char* rec) {
   const int N = p.N;
   const int* D = slot_dims(slot);
@@ -234,12 +250,12 @@ __device__ void pack_state(const TrajParams& p, const Lay& Y, const unsigned cha
     for (int i = 0; i <= N; ++i) hd[i] = D[i];
     for (int i = 0; i < N; ++i) {
       hd[N + 1 + i] = o;
-      o += D[i] * 2 * D[i + 1];
+      o += D[i] * kD * D[i + 1];
     }
   }
   size_t o = 0;
   for (int i = 0; i < N; ++i) {
-    const int cnt = D[i] * 2 * D[i + 1];
+    const int cnt = D[i] * kD * D[i + 1];
     const double2* a = src + Y.site_off[i];
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) out[o + e] = a[e];
     o += cnt;
@@ -252,9 +268,10 @@ __device__ void pack_state(const TrajParams& p, const Lay& Y, const unsigned cha
 // Left:  Eout[b'][a'] = sum_{b,s,a} conj(c[b][s][b']) Ein[b][a] a[a][s][a']
 // Right: Eout[b][a]   = sum_{s,b',a'} conj(c[b][s][b']) Ein[b'][a'] a[a][s][a']
 // ---------------------------------------------------------------------------
+template <int kD>
 __device__ void env_left_step(const double2* Ein, int Dcl, int Dal, const double2* c, int Dcr,
                               const double2* a, int Dar, double2* tmp, double2* Eout, int lane) {
-  const int w2 = 2 * Dar;
+  const int w2 = kD * Dar;
   for (int it = lane; it < Dcl * w2; it += 32) {
     const int be = it / w2, rest = it - be * w2;
     double2 acc = make_double2(0.0, 0.0);
@@ -267,21 +284,22 @@ __device__ void env_left_step(const double2* Ein, int Dcl, int Dal, const double
     double2 acc = make_double2(0.0, 0.0);
     for (int be = 0; be < Dcl; ++be)
 #pragma unroll
-      for (int s = 0; s < 2; ++s)
-        cfmac(acc, c[(size_t)be * 2 * Dcr + s * Dcr + bp], tmp[(size_t)be * w2 + s * Dar + ap]);
+      for (int s = 0; s < kD; ++s)
+        cfmac(acc, c[(size_t)be * kD * Dcr + s * Dcr + bp], tmp[(size_t)be * w2 + s * Dar + ap]);
     Eout[it] = acc;
   }
   __syncwarp();
 }
 
+template <int kD>
 __device__ void env_right_step(const double2* Ein, int Dcr, int Dar, const double2* c, int Dcl,
                                const double2* a, int Dal, double2* tmp, double2* Eout, int lane) {
-  const int w2 = 2 * Dal;
+  const int w2 = kD * Dal;
   for (int it = lane; it < Dcr * w2; it += 32) {
     const int bp = it / w2, rest = it - bp * w2;
     const int s = rest / Dal, al = rest - s * Dal;
     double2 acc = make_double2(0.0, 0.0);
-    for (int ap = 0; ap < Dar; ++ap) cfma(acc, Ein[bp * Dar + ap], a[(size_t)al * 2 * Dar + s * Dar + ap]);
+    for (int ap = 0; ap < Dar; ++ap) cfma(acc, Ein[bp * Dar + ap], a[(size_t)al * kD * Dar + s * Dar + ap]);
     tmp[it] = acc;
   }
   __syncwarp();
@@ -290,14 +308,15 @@ __device__ void env_right_step(const double2* Ein, int Dcr, int Dar, const doubl
     double2 acc = make_double2(0.0, 0.0);
     for (int bp = 0; bp < Dcr; ++bp)
 #pragma unroll
-      for (int s = 0; s < 2; ++s)
-        cfmac(acc, c[(size_t)be * 2 * Dcr + s * Dcr + bp], tmp[(size_t)bp * w2 + s * Dal + al]);
+      for (int s = 0; s < kD; ++s)
+        cfmac(acc, c[(size_t)be * kD * Dcr + s * Dcr + bp], tmp[(size_t)bp * w2 + s * Dal + al]);
     Eout[it] = acc;
   }
   __syncwarp();
 }
 
 // <t|a> by one warp.
+template <int kD>
 __device__ double2 warp_overlap(const TrajParams& p, const Lay& Yt, const unsigned char* tslot, const Lay& Ya,
                                 const unsigned char* aslot, WarpCtx& w) {
   const int* Dt = slot_dims(tslot);
@@ -311,8 +330,8 @@ __device__ double2 warp_overlap(const TrajParams& p, const Lay& Yt, const unsign
   if (w.lane == 0) E0[0] = make_double2(1.0, 0.0);
   __syncwarp();
   for (int i = 0; i < p.N; ++i) {
-    env_left_step(E0, Dt[i], Da[i], ts + Yt.site_off[i], Dt[i + 1], as + Ya.site_off[i], Da[i + 1], tmp, E1,
-                  w.lane);
+    env_left_step<kD>(E0, Dt[i], Da[i], ts + Yt.site_off[i], Dt[i + 1], as + Ya.site_off[i], Da[i + 1], tmp, E1,
+                      w.lane);
     double2* x = E0;
     E0 = E1;
     E1 = x;
@@ -325,8 +344,10 @@ __device__ double2 warp_overlap(const TrajParams& p, const Lay& Yt, const unsign
 // dO/du = tr(Q_u rho) for every control u of every gate in the layer, added
 // to the trajectory's gradient row as 2 Re(conj(O) dO/du).
 // ---------------------------------------------------------------------------
+template <int kD>
 __device__ void layer_gradient(const TrajParams& p, const Lay& Y, const unsigned char* cslot, const StateView av,
                                int s, int l, double2 wO, double* gsp_row, WarpCtx& w, int warp) {
+  constexpr int kDD = kD * kD, kI = kD / 2;
   const int parity = layer_parity(p, l);
   const int N = p.N, chi = p.chi;
   const size_t cc = (size_t)chi * chi;
@@ -346,17 +367,17 @@ __device__ void layer_gradient(const TrajParams& p, const Lay& Y, const unsigned
     if (lane == 0) Lbuf[0] = make_double2(1.0, 0.0);
     __syncwarp();
     for (int i = 0; i + 1 <= N - 2; ++i) {
-      env_left_step(Lbuf + i * cc, Dc[i], Da[i], cs + so[i], Dc[i + 1], as + ao[i], Da[i + 1],
-                    w.scratch, Lbuf + (i + 1) * cc, lane);
-      w.alg += 16ull * Da[i + 1] * (unsigned long long)(Dc[i] * Da[i] + Dc[i + 1] * Dc[i]);
+      env_left_step<kD>(Lbuf + i * cc, Dc[i], Da[i], cs + so[i], Dc[i + 1], as + ao[i], Da[i + 1],
+                        w.scratch, Lbuf + (i + 1) * cc, lane);
+      w.alg += 8ull * kD * Da[i + 1] * (unsigned long long)(Dc[i] * Da[i] + Dc[i + 1] * Dc[i]);
     }
   } else if (warp == 1) {
     if (lane == 0) Rbuf[(size_t)N * cc] = make_double2(1.0, 0.0);
     __syncwarp();
     for (int i = N - 1; i >= 2; --i) {
-      env_right_step(Rbuf + (size_t)(i + 1) * cc, Dc[i + 1], Da[i + 1], cs + so[i], Dc[i],
-                     as + ao[i], Da[i], w.scratch, Rbuf + (size_t)i * cc, lane);
-      w.alg += 16ull * Da[i] * (unsigned long long)(Dc[i + 1] * Da[i + 1] + Dc[i] * Dc[i + 1]);
+      env_right_step<kD>(Rbuf + (size_t)(i + 1) * cc, Dc[i + 1], Da[i + 1], cs + so[i], Dc[i],
+                         as + ao[i], Da[i], w.scratch, Rbuf + (size_t)i * cc, lane);
+      w.alg += 8ull * kD * Da[i] * (unsigned long long)(Dc[i + 1] * Da[i + 1] + Dc[i] * Dc[i + 1]);
     }
   }
   __syncthreads();
@@ -374,59 +395,68 @@ __device__ void layer_gradient(const TrajParams& p, const Lay& Y, const unsigned
     const double2* a1 = as + ao[b + 1];
     const double2* c0 = cs + so[b];
     const double2* c1 = cs + so[b + 1];
-    w.alg += 8ull * dcl * (2ull * dam * dal + 4ull * dcr * dcm + 4ull * dar * dam + 4ull * dcr * dar + 16ull * dcr) +
-             2048ull;
-    double2* U1 = w.scratch;                        // [dcl][2][dam]
-    double2* U2 = U1 + 2 * cc;                      // [dcl][4][dar]
-    double2* U3 = U2 + 4 * cc;                      // [dcl][4][dcr]
-    double2* Wc = U3 + 4 * cc;                      // [dcl][4][dcr]
-    for (int it = lane; it < dcl * 2 * dam; it += 32) {
-      const int be = it / (2 * dam), rest = it - be * 2 * dam;
+    w.alg += 8ull * dcl * (kD * dam * dal + kDD * dcr * dcm + kDD * dar * dam + kDD * dcr * dar +
+                           (unsigned long long)kDD * kDD * dcr) + 2048ull;
+    double2* U1 = w.scratch;                        // [dcl][kD][dam]
+    double2* U2 = U1 + kD * cc;                     // [dcl][kD^2][dar]
+    double2* U3 = U2 + kDD * cc;                    // [dcl][kD^2][dcr]
+    double2* Wc = U3 + kDD * cc;                    // [dcl][kD^2][dcr]
+    for (int it = lane; it < dcl * kD * dam; it += 32) {
+      const int be = it / (kD * dam), rest = it - be * kD * dam;
       double2 acc = make_double2(0.0, 0.0);
-      for (int al = 0; al < dal; ++al) cfma(acc, L[be * dal + al], a0[(size_t)al * 2 * dam + rest]);
+      for (int al = 0; al < dal; ++al) cfma(acc, L[be * dal + al], a0[(size_t)al * kD * dam + rest]);
       U1[it] = acc;
     }
-    for (int it = lane; it < dcl * 4 * dcr; it += 32) {
-      const int be = it / (4 * dcr), rest = it - be * 4 * dcr;
+    for (int it = lane; it < dcl * kDD * dcr; it += 32) {
+      const int be = it / (kDD * dcr), rest = it - be * kDD * dcr;
       const int ss = rest / dcr, b2 = rest - ss * dcr;
-      const int s1 = ss >> 1, s2 = ss & 1;
+      const int s1 = ss / kD, s2 = ss % kD;
       double2 acc = make_double2(0.0, 0.0);
       for (int b1 = 0; b1 < dcm; ++b1)
-        cfma(acc, c0[(size_t)be * 2 * dcm + s1 * dcm + b1], c1[(size_t)b1 * 2 * dcr + s2 * dcr + b2]);
+        cfma(acc, c0[(size_t)be * kD * dcm + s1 * dcm + b1], c1[(size_t)b1 * kD * dcr + s2 * dcr + b2]);
       Wc[it] = acc;
     }
     __syncwarp();
-    for (int it = lane; it < dcl * 4 * dar; it += 32) {
-      const int be = it / (4 * dar), rest = it - be * 4 * dar;
+    for (int it = lane; it < dcl * kDD * dar; it += 32) {
+      const int be = it / (kDD * dar), rest = it - be * kDD * dar;
       const int ss = rest / dar, a2 = rest - ss * dar;
-      const int s1 = ss >> 1, s2 = ss & 1;
+      const int s1 = ss / kD, s2 = ss % kD;
       double2 acc = make_double2(0.0, 0.0);
       for (int a1i = 0; a1i < dam; ++a1i)
-        cfma(acc, U1[(size_t)be * 2 * dam + s1 * dam + a1i], a1[(size_t)a1i * 2 * dar + s2 * dar + a2]);
+        cfma(acc, U1[(size_t)be * kD * dam + s1 * dam + a1i], a1[(size_t)a1i * kD * dar + s2 * dar + a2]);
       U2[it] = acc;
     }
     __syncwarp();
-    for (int it = lane; it < dcl * 4 * dcr; it += 32) {
-      const int be = it / (4 * dcr), rest = it - be * 4 * dcr;
+    for (int it = lane; it < dcl * kDD * dcr; it += 32) {
+      const int be = it / (kDD * dcr), rest = it - be * kDD * dcr;
       const int ss = rest / dcr, b2 = rest - ss * dcr;
       double2 acc = make_double2(0.0, 0.0);
-      const double2* u2 = U2 + (size_t)be * 4 * dar + ss * dar;
+      const double2* u2 = U2 + (size_t)be * kDD * dar + ss * dar;
       const double2* rr = R + (size_t)b2 * dar;
       for (int a2 = 0; a2 < dar; ++a2) cfma(acc, u2[a2], rr[a2]);
       U3[it] = acc;
     }
     __syncwarp();
-    // rho[s'][s] = sum_{be,b2} U3[be][s'][b2] conj(Wc[be][s][b2]); lane = (s', s) pair, 16 lanes x 2 halves
+    // rho[o'][o] = sum_{i1,i2} sum_{be,b2} U3[be][s'][b2] conj(Wc[be][s][b2]) over the
+    // two-site out indices o (the in indices, if any, traced out: the gate acts
+    // as Q (x) I); lane = (o', o) pair, 16 lanes x 2 halves
     double2* rho = w.small;
     {
       const int o = lane & 15, half = lane >> 4;
-      const int sp = o >> 2, sq = o & 3;
+      const int op = o >> 2, oq = o & 3;
       double2 acc = make_double2(0.0, 0.0);
-      for (int be = half; be < dcl; be += 2) {
-        const double2* u = U3 + (size_t)be * 4 * dcr + sp * dcr;
-        const double2* wv = Wc + (size_t)be * 4 * dcr + sq * dcr;
-        for (int b2 = 0; b2 < dcr; ++b2) cfmac(acc, wv[b2], u[b2]);
-      }
+#pragma unroll
+      for (int i1 = 0; i1 < kI; ++i1)
+#pragma unroll
+        for (int i2 = 0; i2 < kI; ++i2) {
+          const int sp = ((op >> 1) * kI + i1) * kD + (op & 1) * kI + i2;
+          const int sq = ((oq >> 1) * kI + i1) * kD + (oq & 1) * kI + i2;
+          for (int be = half; be < dcl; be += 2) {
+            const double2* u = U3 + (size_t)be * kDD * dcr + sp * dcr;
+            const double2* wv = Wc + (size_t)be * kDD * dcr + sq * dcr;
+            for (int b2 = 0; b2 < dcr; ++b2) cfmac(acc, wv[b2], u[b2]);
+          }
+        }
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
       if (lane < 16) rho[o] = acc;
@@ -455,6 +485,7 @@ __device__ void layer_gradient(const TrajParams& p, const Lay& Y, const unsigned
 // ---------------------------------------------------------------------------
 // Copy the used part of a state slot; src and dst may use different layouts.
 // Returns 1 (and copies nothing) when a dimension exceeds dst's capacity.
+template <int kD>
 __device__ int copy_slot(const TrajParams& p, const Lay& Ys, const unsigned char* src, const Lay& Yd,
                          unsigned char* dst) {
   __syncthreads();
@@ -474,7 +505,7 @@ __device__ int copy_slot(const TrajParams& p, const Lay& Ys, const unsigned char
   const double2* ss = slot_sites(src, Ys.L);
   double2* sd = slot_sites(dst, Yd.L);
   for (int i = 0; i < p.N; ++i) {
-    const int cnt = Ds[i] * 2 * Ds[i + 1];
+    const int cnt = Ds[i] * kD * Ds[i + 1];
     const double2* a = ss + Ys.site_off[i];
     double2* b = sd + Yd.site_off[i];
     for (int e = tid; e < cnt; e += nt) b[e] = a[e];
@@ -494,6 +525,7 @@ __device__ __forceinline__ long long update_cost(int Dl, int Dr) {
 // in decreasing order of cost (largest SVD first), so that they reach the
 // layer barrier together; a bond's result does not depend on which warp
 // computes it.
+template <int kD>
 __device__ void apply_layer(const TrajParams& p, const Lay& Y, unsigned char* slot, int s, int l, bool adjoint,
                             bool record, bool count, WarpCtx& w, int warp) {
   const int parity = layer_parity(p, l);
@@ -519,7 +551,7 @@ __device__ void apply_layer(const TrajParams& p, const Lay& Y, unsigned char* sl
     j = __shfl_sync(0xffffffffu, j, 0);
     if (j >= nb) break;
     const int b = w.order[j];
-    two_site_update(p, Y, slot, b, layer_rec(p, s, l, b).G, adjoint, record, count, w);
+    two_site_update<kD>(p, Y, slot, b, layer_rec(p, s, l, b).G, adjoint, record, count, w);
   }
   TNRC_TIC(t_b);
   __syncthreads();
@@ -532,6 +564,7 @@ __device__ void apply_layer(const TrajParams& p, const Lay& Y, unsigned char* sl
 //                   sweep); returns 1 if the history outgrows the region.
 //   packed = false: checkpoints every Y.seg layers and recomputation of each
 //                   segment (fits by construction).
+template <int kD>
 __device__ int run_trajectory(const TrajParams& p, bool packed, unsigned char* base, int t, int s, int pi,
                               WarpCtx& w, int warp, double* s_disc, int* s_maxk, double2* s_O) {
   const Lay& Y = p.full;
@@ -548,35 +581,35 @@ __device__ int run_trajectory(const TrajParams& p, bool packed, unsigned char* b
   const int KCN = p.K * p.C * p.N;
   w.disc = 0.0;
   w.maxk = 0;
-  copy_slot(p, Y, p.in_slots + (size_t)pi * sb, Y, a_slot);
+  copy_slot<kD>(p, Y, p.in_slots + (size_t)pi * sb, Y, a_slot);
   // ---- forward ----
   size_t pos = 0;
   for (int l = 0; l < L; ++l) {
     const int q = l / Y.seg;
-    if (p.want_grad && !packed && (l % Y.seg) == 0 && q < Y.nseg - 1) copy_slot(p, Y, a_slot, Y, ckpt + (size_t)q * sb);
-    apply_layer(p, Y, a_slot, s, l, false, true, true, w, warp);
+    if (p.want_grad && !packed && (l % Y.seg) == 0 && q < Y.nseg - 1) copy_slot<kD>(p, Y, a_slot, Y, ckpt + (size_t)q * sb);
+    apply_layer<kD>(p, Y, a_slot, s, l, false, true, true, w, warp);
     if (p.want_grad) {
       if (packed) {
-        const size_t need = packed_bytes(slot_dims(a_slot), p.N);
+        const size_t need = packed_bytes<kD>(slot_dims(a_slot), p.N);
         if (pos + need > hbytes) return 1;
         TNRC_TIC(t_h);
-        pack_state(p, Y, a_slot, harena + pos);
+        pack_state<kD>(p, Y, a_slot, harena + pos);
         TNRC_TOC(w, 6, t_h);
         if (threadIdx.x == 0) hpos[l] = (long long)pos;
         pos += (need + 255) / 256 * 256;
       } else if (q == Y.nseg - 1) {
-        copy_slot(p, Y, a_slot, Y, segs + (size_t)(l - q * Y.seg) * sb);
+        copy_slot<kD>(p, Y, a_slot, Y, segs + (size_t)(l - q * Y.seg) * sb);
       }
     }
   }
   const unsigned char* tg = p.tg_slots + (size_t)pi * sb;
   if (warp == 0) {
-    const double2 O = warp_overlap(p, Y, tg, Y, a_slot, w);
+    const double2 O = warp_overlap<kD>(p, Y, tg, Y, a_slot, w);
     if (lane == 0) *s_O = O;
     const int* Dt = slot_dims(tg);
     const int* Da = slot_dims(a_slot);
     for (int i = 0; i < p.N; ++i)
-      w.alg += 16ull * Da[i + 1] * (unsigned long long)(Dt[i] * Da[i] + Dt[i + 1] * Dt[i]);
+      w.alg += 8ull * kD * Da[i + 1] * (unsigned long long)(Dt[i] * Da[i] + Dt[i + 1] * Dt[i]);
   }
   if (lane == 0) {
     s_disc[warp] = w.disc;
@@ -599,11 +632,11 @@ __device__ int run_trajectory(const TrajParams& p, bool packed, unsigned char* b
   // ---- costate sweep ----
   double* grow = p.gsp + (size_t)t * KCN;
   for (int i = threadIdx.x; i < KCN; i += blockDim.x) grow[i] = 0.0;
-  copy_slot(p, Y, tg, Y, c_slot);
+  copy_slot<kD>(p, Y, tg, Y, c_slot);
   if (packed) {
     for (int l = L - 1; l >= 0; --l) {
-      layer_gradient(p, Y, c_slot, packed_view(harena + hpos[l], p.N), s, l, O, grow, w, warp);
-      apply_layer(p, Y, c_slot, s, l, true, false, true, w, warp);
+      layer_gradient<kD>(p, Y, c_slot, packed_view(harena + hpos[l], p.N), s, l, O, grow, w, warp);
+      apply_layer<kD>(p, Y, c_slot, s, l, true, false, true, w, warp);
     }
     return 0;
   }
@@ -613,13 +646,13 @@ __device__ int run_trajectory(const TrajParams& p, bool packed, unsigned char* b
     if (q != Y.nseg - 1) {
       unsigned char* ck = ckpt + (size_t)q * sb;
       for (int l = l0; l < l1; ++l) {
-        apply_layer(p, Y, ck, s, l, false, false, false, w, warp);
-        copy_slot(p, Y, ck, Y, segs + (size_t)(l - l0) * sb);
+        apply_layer<kD>(p, Y, ck, s, l, false, false, false, w, warp);
+        copy_slot<kD>(p, Y, ck, Y, segs + (size_t)(l - l0) * sb);
       }
     }
     for (int l = l1 - 1; l >= l0; --l) {
-      layer_gradient(p, Y, c_slot, slot_view(segs + (size_t)(l - l0) * sb, Y), s, l, O, grow, w, warp);
-      apply_layer(p, Y, c_slot, s, l, true, false, true, w, warp);
+      layer_gradient<kD>(p, Y, c_slot, slot_view(segs + (size_t)(l - l0) * sb, Y), s, l, O, grow, w, warp);
+      apply_layer<kD>(p, Y, c_slot, s, l, true, false, true, w, warp);
     }
   }
   return 0;
@@ -628,7 +661,7 @@ __device__ int run_trajectory(const TrajParams& p, bool packed, unsigned char* b
 // Compiled twice: kMinBlocks = 1 lets a thread use up to 255 registers (at
 // most 8 warps per SM); kMinBlocks = 2 caps it at 128 so that 16 warps fit an
 // SM, trading a few spilled values for twice the warps to hide FP64 latency.
-template <int kMinBlocks>
+template <int kMinBlocks, int kD>
 __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) traj_kernel(TrajParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
@@ -674,7 +707,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) traj_kernel(TrajParam
     if (p.want_grad && p.packed_history) {
       const long long sw0 = w.sweeps, up0 = w.updates;
       const unsigned long long al0 = w.alg;
-      redo = run_trajectory(p, true, base, t, s, pi, w, warp, s_disc, s_maxk, &s_O) != 0;
+      redo = run_trajectory<kD>(p, true, base, t, s, pi, w, warp, s_disc, s_maxk, &s_O) != 0;
       if (redo) {  // history outgrew the region: discard the attempt's counts, count the fallback
         w.sweeps = sw0;
         w.updates = up0;
@@ -682,7 +715,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) traj_kernel(TrajParam
         if (threadIdx.x == 0) atomicAdd(&p.counters[4], 1ull);
       }
     }
-    if (redo) run_trajectory(p, false, base, t, s, pi, w, warp, s_disc, s_maxk, &s_O);
+    if (redo) run_trajectory<kD>(p, false, base, t, s, pi, w, warp, s_disc, s_maxk, &s_O);
   }
   if (lane == 0) {
     atomicAdd(&p.counters[0], (unsigned long long)w.updates);
@@ -704,19 +737,24 @@ extern "C" cudaError_t tnrc_traj_prepare() {
   if (e != cudaSuccess) return e;
   static bool attr_set[64] = {false};
   if (dev >= 0 && dev < 64 && attr_set[dev]) return cudaSuccess;
-  e = cudaFuncSetAttribute(tnrc::traj_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  e = cudaFuncSetAttribute(tnrc::traj_kernel<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(tnrc::traj_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+    e = cudaFuncSetAttribute(tnrc::traj_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tnrc::traj_kernel<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
   if (e == cudaSuccess && dev >= 0 && dev < 64) attr_set[dev] = true;
   return e;
 }
 
 extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, size_t smem, cudaStream_t st) {
   (void)cudaGetLastError();  // report only this launch below
-  if (p->min_blocks == 2)
-    tnrc::traj_kernel<2><<<grid, p->warps * 32, smem, st>>>(*p);
+  // operators (physical dimension 4) run the 255-register build only
+  if (p->phys_dim == 4)
+    tnrc::traj_kernel<1, 4><<<grid, p->warps * 32, smem, st>>>(*p);
+  else if (p->min_blocks == 2)
+    tnrc::traj_kernel<2, 2><<<grid, p->warps * 32, smem, st>>>(*p);
   else
-    tnrc::traj_kernel<1><<<grid, p->warps * 32, smem, st>>>(*p);
+    tnrc::traj_kernel<1, 2><<<grid, p->warps * 32, smem, st>>>(*p);
   return cudaGetLastError();
 }
 

@@ -37,7 +37,8 @@ class Problem(ctypes.Structure):
                 ("control_mask", ctypes.POINTER(ctypes.c_uint8)), ("g_fixed", ctypes.POINTER(ctypes.c_double)),
                 ("checkpoint_every", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("crosstalk_terms", ctypes.c_int32),
-                ("trotter_order", ctypes.c_int32), ("substeps", ctypes.c_int32)]
+                ("trotter_order", ctypes.c_int32), ("substeps", ctypes.c_int32),
+                ("operator_form", ctypes.c_int32)]
 
 
 class MPSDesc(ctypes.Structure):
@@ -134,7 +135,7 @@ def _pack(state):
 
 
 def make_problem(N, K, dt, chi, M, C, P, cutoff=1e-12, mask=None, g_fixed=None, checkpoint_every=0, warps=0,
-                 ctas_per_sm=0, crosstalk=1, order=2, substeps=1):
+                 ctas_per_sm=0, crosstalk=1, order=2, substeps=1, operator=False):
     """A ``Problem`` plus the arrays it points to (keep both alive)."""
     keep = []
     pb = Problem()
@@ -155,6 +156,7 @@ def make_problem(N, K, dt, chi, M, C, P, cutoff=1e-12, mask=None, g_fixed=None, 
     pb.crosstalk_terms = crosstalk
     pb.trotter_order = order
     pb.substeps = substeps
+    pb.operator_form = 1 if operator else 0
     return pb, keep
 
 
@@ -169,7 +171,7 @@ def _descs(states):
 
 
 def fidelity_static(N, K, dt, chi, C, inputs, targets, u, J, cutoff=1e-12, mask=None, g_fixed=None,
-                    stream=None, per_traj=False, crosstalk=1, order=2, substeps=1):
+                    stream=None, per_traj=False, crosstalk=1, order=2, substeps=1, operator=False):
     """F (and per-trajectory |O|^2) through tnrc_fidelity_static, which
     allocates no device memory: for callers that cannot call cudaMalloc.
     Calls must not overlap on the GPU (they share one static array)."""
@@ -177,7 +179,7 @@ def fidelity_static(N, K, dt, chi, C, inputs, targets, u, J, cutoff=1e-12, mask=
     u = np.ascontiguousarray(u, dtype=np.float64)
     M, P = J.shape[0], len(inputs)
     pb, keep = make_problem(N, K, dt, chi, M, C, P, cutoff, mask, g_fixed, crosstalk=crosstalk, order=order,
-                            substeps=substeps)
+                            substeps=substeps, operator=operator)
     ins, kin = _descs(inputs)
     tgs, ktg = _descs(targets)
     F = np.zeros(1)
@@ -206,7 +208,7 @@ class Context:
     def __init__(self, N: int, K: int, dt: float, chi: int, M: int, C: int, inputs: Sequence, targets: Sequence,
                  cutoff: float = 1e-12, mask=None, g_fixed=None, checkpoint_every: int = 0,
                  stream: Optional[int] = None, warps: int = 0, ctas_per_sm: int = 0, crosstalk: int = 1,
-                 order: int = 2, substeps: int = 1):
+                 order: int = 2, substeps: int = 1, operator: bool = False):
         L = lib()
         self.N, self.K, self.C, self.M, self.P = N, K, C, M, len(inputs)
         self.stream = int(stream or 0)
@@ -214,7 +216,7 @@ class Context:
         if len(targets) != self.P:
             raise ValueError("inputs and targets differ in length")
         pb, keep = make_problem(N, K, dt, chi, M, C, self.P, cutoff, mask, g_fixed, checkpoint_every, warps,
-                                ctas_per_sm, crosstalk, order, substeps)
+                                ctas_per_sm, crosstalk, order, substeps, operator)
         packs = [_pack(s) for s in list(inputs) + list(targets)]
         descs = (MPSDesc * len(packs))()
         for d, (dims, data) in zip(descs, packs):

@@ -21,7 +21,7 @@ def gpu_context(w, inputs, targets, mask, g_fixed=None, checkpoint_every=0, warp
     from paper_2603_03639_gb300 import Context
     return Context(w.N, w.K, w.dt, w.chi, w.M, w.C, inputs, targets, cutoff=w.sv_cutoff, mask=mask,
                    g_fixed=g_fixed, checkpoint_every=checkpoint_every, crosstalk=w.crosstalk, warps=warps,
-                   ctas_per_sm=ctas_per_sm, order=w.order, substeps=w.substeps)
+                   ctas_per_sm=ctas_per_sm, order=w.order, substeps=w.substeps, operator=w.operator)
 
 
 def case(w, u=None):

@@ -131,6 +131,23 @@ def test_first_order_heisenberg_crosstalk_truncated():
     assert grad_close(g, go)
 
 
+@pytest.mark.parametrize("target,order,terms,N,chi", [("cnot", 2, 1, 8, 16), ("x", 2, 3, 7, 16), ("cnot", 1, 3, 8, 16),
+                                                      ("cnot", 2, 1, 10, 4), ("x", 1, 1, 5, 8)])
+def test_operator_form_parity(target, order, terms, N, chi):
+    """The MPO of Sec. II (operators as vectors, physical dimension 4) from the
+    identity: the gate fidelity |tr(U_T^dag U) / 2^N|^2 of Eq. gateinfid, its
+    gradient and the per-sample overlaps against the oracle, untruncated and
+    truncated (chi = 4)."""
+    w = synth.WORKLOADS["cnotgate50"].replace(N=N, K=4, chi=chi, M=3, P=1, target=target, order=order,
+                                              crosstalk=terms, g_bonds="pairs" if target == "cnot" else "all")
+    # near the pi pulse the X-gate fidelity is O(1) (random controls give ~0)
+    u = synth.pi_pulse_controls(w.K, w.C, w.N, w.dt, seed=5, jitter=0.1) if target == "x" else None
+    _, (F, g, O), (Fo, go, Oo) = run_both(w, u=u)
+    assert abs(F - Fo) <= TOL_F
+    assert np.max(np.abs(O - Oo)) <= TOL_O
+    assert grad_close(g, go)
+
+
 def test_checkpoint_segments_do_not_change_results(monkeypatch):
     """Checkpoint/recompute segmentations (history cap 0 forces that path) and
     the packed history give bitwise the same result."""

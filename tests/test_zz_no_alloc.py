@@ -22,24 +22,26 @@ def _case(w):
     return ins, tgs, u, J, w.mask()
 
 
-@pytest.mark.parametrize("name", ["x8", "cnot_small", "first_order"])
+@pytest.mark.parametrize("name", ["x8", "cnot_small", "first_order", "operator"])
 def test_static_scratch_matches_allocating_path_twice(name):
     from paper_2603_03639_gb300 import Context, tnrc
     if name == "x8":
         w = synth.WORKLOADS["x8"]
     elif name == "first_order":
         w = synth.WORKLOADS["cnot50"].replace(N=10, K=6, chi=16, M=4, P=2, order=1, substeps=2)
+    elif name == "operator":
+        w = synth.WORKLOADS["cnotgate50"].replace(N=8, K=5, chi=8, M=4)
     else:
         w = synth.WORKLOADS["cnot50"].replace(N=10, K=8, chi=16, M=6, P=3)
     ins, tgs, u, J, mask = _case(w)
     with Context(w.N, w.K, w.dt, w.chi, w.M, w.C, ins, tgs, cutoff=w.sv_cutoff, mask=mask, order=w.order,
-                 substeps=w.substeps) as ctx:
+                 substeps=w.substeps, operator=w.operator) as ctx:
         ctx.set_controls(u)
         ctx.set_noise(J)
         F_ref, pt_ref = ctx.fidelity(per_traj=True)
     for _ in range(2):
         F, pt = tnrc.fidelity_static(w.N, w.K, w.dt, w.chi, w.C, ins, tgs, u, J, cutoff=w.sv_cutoff, mask=mask,
-                                     per_traj=True, order=w.order, substeps=w.substeps)
+                                     per_traj=True, order=w.order, substeps=w.substeps, operator=w.operator)
         assert abs(F - F_ref) <= TOL_F
         assert np.max(np.abs(pt - pt_ref)) <= TOL_O
 
