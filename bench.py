@@ -224,7 +224,7 @@ def gpu_arm(args, w):
     mask = w.mask()
     u = w.controls()
     from paper_2603_03639_gb300 import autotune
-    tuned = autotune.lookup(w.N, w.K, w.chi, w.M, w.P, w.C, grad=True)
+    tuned = autotune.lookup(w.N, w.K, w.chi, w.M, w.P, w.C, grad=True, operator=w.operator)
     ctx = Context(w.N, w.K, w.dt, w.chi, w.M, w.C, ins, tgs, cutoff=w.sv_cutoff, mask=mask,
                   stream=stream.cuda_stream, warps=tuned[0], ctas_per_sm=tuned[1], **form_kwargs(w))
     u_dev = torch.tensor(u, dtype=torch.float64, device=dev)
@@ -453,7 +453,7 @@ def plain_arm(args, w):
 
     ws = w.replace(M=args.plain_samples)
     ins, tgs = ws.states()
-    tuned = autotune.lookup(w.N, w.K, w.chi, w.M, w.P, w.C, grad=True)
+    tuned = autotune.lookup(w.N, w.K, w.chi, w.M, w.P, w.C, grad=True, operator=w.operator)
     out = {}
     for mode in ("batched", "plain"):
         if mode == "plain":

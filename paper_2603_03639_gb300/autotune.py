@@ -23,10 +23,12 @@ QUICK = [(8, 1), (4, 2), (3, 2), (8, 2), (4, 4)]
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
 
-def shape_key(N, K, chi, M, P, C, grad=True):
-    """Shape bucket: N and C exactly; K, M*P and chi by powers of two."""
+def shape_key(N, K, chi, M, P, C, grad=True, operator=False):
+    """Shape bucket: N and C exactly; K, M*P and chi by powers of two; the
+    operator form (physical dimension 4) apart."""
     b = lambda x: 1 << int(np.ceil(np.log2(max(1, x))))  # noqa: E731
-    return "N%d-C%d-K%d-T%d-chi%d-%s" % (N, C, b(K), b(M * P), b(chi), "grad" if grad else "fid")
+    return "N%d-C%d-K%d-T%d-chi%d-%s%s" % (N, C, b(K), b(M * P), b(chi), "grad" if grad else "fid",
+                                         "-op" if operator else "")
 
 
 def load(path=None):
@@ -38,11 +40,11 @@ def load(path=None):
         return {}
 
 
-def lookup(N, K, chi, M, P, C, grad=True, path=None):
+def lookup(N, K, chi, M, P, C, grad=True, path=None, operator=False):
     """(warps_per_cta, ctas_per_sm) cached for this shape -- or for the same
     shape with the nearest ensemble-size bucket -- else (0, 0) (defaults)."""
     cache = load(path)
-    key = shape_key(N, K, chi, M, P, C, grad)
+    key = shape_key(N, K, chi, M, P, C, grad, operator)
     e = cache.get(key)
     if e is None:
         head, tail = key.split("-T")
@@ -56,16 +58,21 @@ def lookup(N, K, chi, M, P, C, grad=True, path=None):
 
 
 def tune(N, K, dt, chi, M, C, inputs, targets, u, noise, mask=None, grad=True, candidates=CANDIDATES, reps=1,
-         stream=None):
-    """Time every candidate; returns (best (warps, ctas), {candidate: ms})."""
+         stream=None, form=None):
+    """Time every candidate; returns (best (warps, ctas), {candidate: ms}).
+    form: Context keywords of the time discretisation and form (crosstalk,
+    order, substeps, operator)."""
     from .tnrc import Context
     seed, dist, scale = noise
+    form = form or {}
     nb = max((N - 1 + 1) // 2, 1)
+    max_warps_per_sm = 8 if form.get("operator") else 16   # operators run the 255-register build only
     times = {}
     for w, c in candidates:
-        if w * c > 16 or w > max(2, nb):
+        if w * c > max_warps_per_sm or w > max(2, nb):
             continue
-        with Context(N, K, dt, chi, M, C, inputs, targets, mask=mask, stream=stream, warps=w, ctas_per_sm=c) as ctx:
+        with Context(N, K, dt, chi, M, C, inputs, targets, mask=mask, stream=stream, warps=w, ctas_per_sm=c,
+                     **form) as ctx:
             ctx.set_controls(u)
             ctx.sample_noise(seed, dist, scale)
             (ctx.fidelity_grad if grad else ctx.fidelity)()          # warm-up
@@ -96,9 +103,11 @@ def main():
     grad = not args.fidelity_only
     best, times = tune(w.N, w.K, w.dt, w.chi, w.M, w.C, ins, tgs, w.controls(),
                        (w.seed_J, w.noise_dist, w.noise_scale), mask=w.mask(), grad=grad,
-                       candidates=QUICK if args.quick else CANDIDATES)
+                       candidates=QUICK if args.quick else CANDIDATES,
+                       form={"crosstalk": w.crosstalk, "order": w.order, "substeps": w.substeps,
+                             "operator": w.operator})
     cache = load(args.out)
-    key = shape_key(w.N, w.K, w.chi, w.M, w.P, w.C, grad)
+    key = shape_key(w.N, w.K, w.chi, w.M, w.P, w.C, grad, w.operator)
     cache[key] = {"warps": best[0], "ctas_per_sm": best[1], "workload": w.name,
                   "ms": {"%dx%d" % k: round(v, 3) for k, v in times.items()}}
     with open(args.out, "w") as f:

@@ -172,7 +172,7 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   w.sweeps += (sw < 0) ? -sw : sw;
   w.updates += 1;
   if (record) {
-    w.disc += (tot2 - kept2) / tot2;
+    w.disc += fmax(0.0, tot2 - kept2) / tot2;   // rounding can make tot2 - kept2 slightly negative
     if (k > w.maxk) w.maxk = k;
     if (lane == 0) atomicAdd(&p.counters[kCtrHist + k], 1ull);
   }
