@@ -92,8 +92,9 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   double* lam = slot_lam(slot, Y.L);
   double2* A = sites + Y.site_off[b];
   double2* Bt = sites + Y.site_off[b + 1];
+  // theta (then R^dagger) and Phi in the warp's shared slab when they fit
   double2* T = (m * n <= p.slab_elems) ? w.slab : (w.scratch + (size_t)kD * kD * chi * chi);
-  double2* Phi = w.scratch;
+  double2* Phi = (2 * m * n <= p.slab_elems) ? w.slab + m * n : w.scratch;
 
   double2 g[16];
 #pragma unroll
@@ -367,16 +368,19 @@ __device__ void layer_gradient(const TrajParams& p, const Lay& Y, const unsigned
     if (lane == 0) Lbuf[0] = make_double2(1.0, 0.0);
     __syncwarp();
     for (int i = 0; i + 1 <= N - 2; ++i) {
+      // the step's intermediate (Dc[i] x kD Da[i+1]) in the warp's shared slab when it fits
+      double2* tmp = (Dc[i] * kD * Da[i + 1] <= p.slab_elems) ? w.slab : w.scratch;
       env_left_step<kD>(Lbuf + i * cc, Dc[i], Da[i], cs + so[i], Dc[i + 1], as + ao[i], Da[i + 1],
-                        w.scratch, Lbuf + (i + 1) * cc, lane);
+                        tmp, Lbuf + (i + 1) * cc, lane);
       w.alg += 8ull * kD * Da[i + 1] * (unsigned long long)(Dc[i] * Da[i] + Dc[i + 1] * Dc[i]);
     }
   } else if (warp == 1) {
     if (lane == 0) Rbuf[(size_t)N * cc] = make_double2(1.0, 0.0);
     __syncwarp();
     for (int i = N - 1; i >= 2; --i) {
+      double2* tmp = (Dc[i + 1] * kD * Da[i] <= p.slab_elems) ? w.slab : w.scratch;
       env_right_step<kD>(Rbuf + (size_t)(i + 1) * cc, Dc[i + 1], Da[i + 1], cs + so[i], Dc[i],
-                         as + ao[i], Da[i], w.scratch, Rbuf + (size_t)i * cc, lane);
+                         as + ao[i], Da[i], tmp, Rbuf + (size_t)i * cc, lane);
       w.alg += 8ull * kD * Da[i] * (unsigned long long)(Dc[i + 1] * Da[i + 1] + Dc[i] * Dc[i + 1]);
     }
   }
@@ -397,10 +401,13 @@ __device__ void layer_gradient(const TrajParams& p, const Lay& Y, const unsigned
     const double2* c1 = cs + so[b + 1];
     w.alg += 8ull * dcl * (kD * dam * dal + kDD * dcr * dcm + kDD * dar * dam + kDD * dcr * dar +
                            (unsigned long long)kDD * kDD * dcr) + 2048ull;
-    double2* U1 = w.scratch;                        // [dcl][kD][dam]
-    double2* U2 = U1 + kD * cc;                     // [dcl][kD^2][dar]
-    double2* U3 = U2 + kDD * cc;                    // [dcl][kD^2][dcr]
-    double2* Wc = U3 + kDD * cc;                    // [dcl][kD^2][dcr]
+    // the four intermediates packed at their actual sizes, in the warp's shared
+    // slab when they fit (the slab is idle outside the two-site update)
+    const int n1 = dcl * kD * dam, n2 = dcl * kDD * dar, n3 = dcl * kDD * dcr;
+    double2* U1 = (n1 + n2 + 2 * n3 <= p.slab_elems) ? w.slab : w.scratch;   // [dcl][kD][dam]
+    double2* U2 = U1 + n1;                          // [dcl][kD^2][dar]
+    double2* U3 = U2 + n2;                          // [dcl][kD^2][dcr]
+    double2* Wc = U3 + n3;                          // [dcl][kD^2][dcr]
     for (int it = lane; it < dcl * kD * dam; it += 32) {
       const int be = it / (kD * dam), rest = it - be * kD * dam;
       double2 acc = make_double2(0.0, 0.0);
