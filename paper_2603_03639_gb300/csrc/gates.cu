@@ -291,12 +291,28 @@ __global__ void layer_gate_kernel(LayerGateArgs a) {
       const int cidx = code & 1, site = b + (code >> 1);
       if (mk[cidx * N + site]) { pc[np] = code; pw[np] = 1.0; pcc[np] = cidx; psite[np++] = site; }
     }
+    // Gam_ij e^{i tau lam_j} = -i tau e^{-i tau (lam_i - lam_j)/2} sinc(tau (lam_i - lam_j)/2):
+    // one sincos per entry, shared by every control of the factor
+    double2 GE[16];
+    {
+      const double tau = ftau[f];
+      const double* lam = lamf[f];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const double x = 0.5 * tau * (lam[i] - lam[j]);
+          double sn, cs;
+          sincos(x, &sn, &cs);
+          const double sinc = (fabs(x) < 1e-8) ? 1.0 - x * x / 6.0 : sn / x;
+          // -i tau sinc (cs - i sn) = tau sinc (-sn - i cs)
+          GE[i * 4 + j] = make_double2(-tau * sinc * sn, -tau * sinc * cs);
+        }
+    }
     for (int q = 0; q < np; ++q) {
       // Q_f = V (Gam o (V^dag P V)) e^{i tau Lam} V^dag  (= dG_f G_f^dag)
       double2 P[16], T1[16], T2[16];
       generator4(pc[q], pw[q], P);
-      const double tau = ftau[f];
-      const double* lam = lamf[f];
       const double2* V = Vf[f];
 #pragma unroll
       for (int i = 0; i < 4; ++i)       // T1 = P V
@@ -314,42 +330,42 @@ __global__ void layer_gate_kernel(LayerGateArgs a) {
           double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
           for (int m = 0; m < 4; ++m) cfmac(acc, V[m * 4 + i], T1[m * 4 + j]);
-          const double x = 0.5 * tau * (lam[i] - lam[j]);
-          const double sinc = (fabs(x) < 1e-8) ? 1.0 - x * x / 6.0 : sin(x) / x;
-          double sn, cs;
-          sincos(0.5 * tau * (lam[i] + lam[j]), &sn, &cs);
-          // -i tau (cs - i sn) sinc = tau sinc (-sn - i cs); times e^{+i tau lam_j}
-          const double2 gam = make_double2(-tau * sinc * sn, -tau * sinc * cs);
-          double se, ce;
-          sincos(tau * lam[j], &se, &ce);
-          T2[i * 4 + j] = cmul(cmul(gam, acc), make_double2(ce, se));
+          T2[i * 4 + j] = cmul(GE[i * 4 + j], acc);
         }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)       // T1 = V T2 V^dag
+      for (int i = 0; i < 4; ++i)       // T1 = T2 V^dag
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            double2 t = make_double2(0.0, 0.0);
-#pragma unroll
-            for (int n2 = 0; n2 < 4; ++n2) cfma(t, T2[m * 4 + n2], cconj(V[j * 4 + n2]));
-            cfma(acc, V[i * 4 + m], t);
-          }
+          for (int m = 0; m < 4; ++m) cfma(acc, T2[i * 4 + m], cconj(V[j * 4 + m]));
           T1[i * 4 + j] = acc;
         }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)       // T2 = Lt T1 Lt^dag
+      for (int i = 0; i < 4; ++i)       // T2 = V T1  (= dG_f G_f^dag)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            double2 t = make_double2(0.0, 0.0);
+          for (int m = 0; m < 4; ++m) cfma(acc, V[i * 4 + m], T1[m * 4 + j]);
+          T2[i * 4 + j] = acc;
+        }
 #pragma unroll
-            for (int n2 = 0; n2 < 4; ++n2) cfma(t, T1[m * 4 + n2], cconj(Lt[j * 4 + n2]));
-            cfma(acc, Lt[i * 4 + m], t);
-          }
+      for (int i = 0; i < 4; ++i)       // T1 = T2 Lt^dag
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) cfma(acc, T2[i * 4 + m], cconj(Lt[j * 4 + m]));
+          T1[i * 4 + j] = acc;
+        }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)       // T2 = Lt T1
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) cfma(acc, Lt[i * 4 + m], T1[m * 4 + j]);
           T2[i * 4 + j] = acc;
         }
       const int slot = (k * a.C + pcc[q]) * N + psite[q];
