@@ -103,3 +103,32 @@ def test_footprint_grows_with_the_problem(L):
     big = tnrc.footprint(50, 100, 0.05, 64, 256, 3, 8)
     assert 0 < small < big
     assert tnrc.footprint(1, 20, 0.05, 16, 16, 2, 4) == 0
+
+
+def test_discretisation_and_form_fields_are_validated(L):
+    """trotter_order, substeps, operator_form, crosstalk_terms and the launch
+    shape are checked on the host: a bad value gives a zero footprint (and
+    TNRC_E_INVALID from tnrc_create) before any device call."""
+    from paper_2603_03639_gb300 import tnrc
+    args = (8, 20, 0.05, 16, 16, 3, 4)
+    assert tnrc.footprint(*args) > 0
+    for kw in (dict(order=3), dict(order=-1), dict(substeps=-1), dict(crosstalk=2), dict(ctas_per_sm=9),
+               dict(warps=9), dict(warps=1)):
+        assert tnrc.footprint(*args, **kw) == 0, kw
+    pb, _ = tnrc.make_problem(*args)
+    pb.operator_form = 2
+    assert L.tnrc_footprint(ctypes.byref(pb)) == 0
+    # operators: theta is 4 chi wide, so chi is capped at 32
+    assert tnrc.footprint(8, 20, 0.05, 32, 16, 3, 1, operator=True) > 0
+    assert tnrc.footprint(8, 20, 0.05, 33, 16, 3, 1, operator=True) == 0
+
+
+def test_footprint_follows_the_discretisation_and_form(L):
+    """More truncated layers (first order: 2 per step; substeps) and the
+    operator form's wider sites need more memory."""
+    from paper_2603_03639_gb300 import tnrc
+    args = (10, 20, 0.05, 16, 16, 3, 2)
+    base = tnrc.footprint(*args)
+    assert tnrc.footprint(*args, substeps=3) > base
+    assert tnrc.footprint(*args, operator=True) > base
+    assert tnrc.footprint(*args, order=1) > 0

@@ -198,6 +198,26 @@ def test_second_order_trotter_error_scaling():
     assert 3.3 < errs[1] / errs[2] < 4.7
 
 
+@pytest.mark.parametrize("order,ratio", [(1, 2.0), (2, 4.0)])
+def test_trotter_error_order_with_substeps(order, ratio):
+    """Against the exact exponential of each bin's Hamiltonian (Eq. sysH), the
+    overlap error of n Trotter steps per bin falls as 1/n for the first-order
+    slice of Eq. circuit and as 1/n^2 for the second-order split."""
+    N, K, T = 4, 2, 1.0
+    rng = np.random.default_rng(57)
+    u = rng.normal(0, 1.0, size=(K, 3, N))
+    J = rng.uniform(-0.5, 0.5, size=N - 1)
+    ins = rand_products(N, 1, 58)
+    tgs = rand_products(N, 1, 59)
+    errs = []
+    for n in (4, 8, 16):
+        pb = mkpb(N, K, T / K, 3, 16, u, synth.control_mask(3, N, "all"), J, ins, tgs, order=order, substeps=n)
+        o_t, _ = robust.trajectory(pb, 0, 0, want_grad=False)
+        errs.append(abs(o_t - dense.exact_overlap(pb, 0, 0)))
+    for a, b in zip(errs, errs[1:]):
+        assert 0.8 * ratio < a / b < 1.2 * ratio, errs
+
+
 # ------------------------------------------------------- finite differences
 def test_gradient_matches_central_finite_differences():
     N, K, dt = 6, 5, 0.1
