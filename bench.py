@@ -3,15 +3,19 @@ GRAPE hot path (ensemble fidelity + costate gradient) on the parallel-CNOT
 workload N = 50, chi_max = 64, K = 100, M = 256, P = 8, C = 3.
 
 One step = one full evaluation through the C ABI on device-resident inputs:
-noise draw (device SplitMix64), gate build, forward TEBD of all M*P
-trajectories with checkpoints, overlaps, costate sweep with environments and
-gradient, and the fixed-order ensemble reduction.  value = M*P*K slice-steps
-per second (whole job; N GPUs each evaluate their own shard of noise samples).
+noise draw (device SplitMix64), layer-gate build, forward TEBD of all M*P
+trajectories (their layer history kept packed), overlaps, costate sweep with
+environments and gradient, and the fixed-order ensemble reduction.
+value = M*P*K slice-steps per second (whole job; N GPUs each evaluate their
+own shard of noise samples).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
 
 --impl reference times the CPU oracle (NumPy/LAPACK) on the host cores on a
-bounded sample of the same workload.
+bounded sample of the same workload.  --plain compares one CTA (one
+trajectory at a time) with the persistent launch on a sample; --serving runs
+the serving rate sweep; --workload picks another shape (x8, x50, ghz30, the
+operator-form cnotgate50); --set KEY=VALUE overrides a field (profiling cases).
 """
 import argparse
 import json
