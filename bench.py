@@ -325,7 +325,9 @@ def gpu_arm(args, w):
                        l2="flushed between timed steps (512 MB write, outside the per-step events)"),
         "e2e": {"value": world * w.slice_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": KCN * 8,
                 "d2h_bytes_per_step": 8 + KCN * 8},
-        "gpu_launches": 6 * args.steps,
+        # per step: noise_kernel, layer_gate_kernel, traj_kernel, reduce_fidelity_kernel,
+        # reduce_grad_kernel (the launch list under profiles/ shows the same five)
+        "gpu_launches": 5 * args.steps,
         "launch_shape": {"warps_per_cta": tuned[0] or "default", "ctas_per_sm": tuned[1] or 1,
                          "source": "autotune cache" if tuned[0] else "default"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
