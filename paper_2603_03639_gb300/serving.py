@@ -55,6 +55,10 @@ class Request:
     want_grad: bool = True
     mask: Optional[np.ndarray] = None
     cutoff: float = 1e-12
+    crosstalk: int = 1            # 1: ZZ; 3: J^x XX + J^y YY + J^z ZZ
+    order: int = 2                # Trotter order (1: the slice of Eq. circuit)
+    substeps: int = 1             # Trotter steps per control bin
+    operator: bool = False        # evolve the operator from the identity (gate objective)
     # filled by the server
     arrival: float = 0.0
     start: float = 0.0
@@ -71,9 +75,14 @@ class Request:
     def latency(self):
         return self.finish - self.arrival
 
+    def form(self):
+        """Context keywords of the request's discretisation and form."""
+        return {"crosstalk": self.crosstalk, "order": self.order, "substeps": self.substeps,
+                "operator": self.operator}
+
     def footprint(self):
         return footprint(self.N, self.K, self.dt, self.chi, self.M, self.C, self.P, cutoff=self.cutoff,
-                         mask=self.mask)
+                         mask=self.mask, **self.form())
 
 
 class _Slot:
@@ -84,7 +93,7 @@ class _Slot:
         self.key = req.key
         self.stream = torch.cuda.Stream(device=device)
         self.ctx = Context(req.N, req.K, req.dt, req.chi, req.M, req.C, req.inputs, req.targets,
-                           cutoff=req.cutoff, mask=req.mask, stream=self.stream.cuda_stream)
+                           cutoff=req.cutoff, mask=req.mask, stream=self.stream.cuda_stream, **req.form())
         self.ctx.set_graphs(True)   # each request replays the context's captured evaluation
         self.bytes = req.footprint()
         self.F = torch.zeros(1, dtype=torch.float64, device=device)

@@ -15,7 +15,9 @@ def _requests(n, seed):
     shapes = [synth.WORKLOADS["x8"].replace(M=8, P=2),
               synth.WORKLOADS["x8"].replace(N=12, chi=16, K=10, M=4, P=2),
               synth.WORKLOADS["cnot50"].replace(N=20, chi=16, K=12, M=6, P=2),
-              synth.WORKLOADS["ghz30"].replace(N=10, chi=8, K=15, M=5, P=1)]
+              synth.WORKLOADS["ghz30"].replace(N=10, chi=8, K=15, M=5, P=1),
+              synth.WORKLOADS["x8"].replace(M=4, P=2, order=1, substeps=2, crosstalk=3),
+              synth.WORKLOADS["cnotgate50"].replace(N=8, chi=8, K=6, M=4)]
     states = [w.states() for w in shapes]
     reqs = []
     for i in range(n):
@@ -25,7 +27,8 @@ def _requests(n, seed):
         reqs.append(Request(key="p%d" % j, N=w.N, K=w.K, dt=w.dt, chi=w.chi, M=w.M, C=w.C, inputs=ins,
                             targets=tgs, controls=rng.normal(0, 0.5, size=(w.K, w.C, w.N)),
                             noise_seed=int(rng.integers(1 << 40)), noise_dist=w.noise_dist,
-                            noise_scale=w.noise_scale, want_grad=bool(i % 2 == 0), mask=w.mask()))
+                            noise_scale=w.noise_scale, want_grad=bool(i % 2 == 0), mask=w.mask(),
+                            crosstalk=w.crosstalk, order=w.order, substeps=w.substeps, operator=w.operator))
     return reqs
 
 
