@@ -223,12 +223,15 @@ def test_state_errors_and_recovery():
 
 @pytest.mark.parametrize("name", ["x50", "cnot50", "ghz30"])
 def test_full_size_sampled_trajectories(name):
-    """Full N, K, chi in the benchmark's launch configuration, reduced to a
-    few noise samples: every overlap against the oracle, and the gradient of
-    a one-trajectory ensemble."""
-    w = synth.WORKLOADS[name].replace(M=2, P=min(2, synth.WORKLOADS[name].P))
+    """Full N, K, chi in the benchmark's launch configuration (the autotuned
+    shape bench.py uses), reduced to a few noise samples: every overlap
+    against the oracle, and the gradient of a one-trajectory ensemble."""
+    from paper_2603_03639_gb300 import autotune
+    w0 = synth.WORKLOADS[name]
+    warps, ctas = autotune.lookup(w0.N, w0.K, w0.chi, w0.M, w0.P, w0.C, grad=True)
+    w = w0.replace(M=2, P=min(2, w0.P))
     u, mask, J, ins, tgs = case(w)
-    ctx = gpu_context(w, ins, tgs, mask)
+    ctx = gpu_context(w, ins, tgs, mask, warps=warps, ctas_per_sm=ctas)
     ctx.set_controls(u)
     ctx.set_noise(J)
     F = ctx.fidelity()
@@ -240,13 +243,37 @@ def test_full_size_sampled_trajectories(name):
             assert abs(O[s, p] - o) <= TOL_O
     w1 = w.replace(M=1, P=1)
     u, mask, J, ins, tgs = case(w1)
-    ctx = gpu_context(w1, ins, tgs, mask)
+    ctx = gpu_context(w1, ins, tgs, mask, warps=warps, ctas_per_sm=ctas)
     ctx.set_controls(u)
     ctx.set_noise(J)
     F, g = ctx.fidelity_grad()
     Fo, go, _ = robust.ensemble(oracle_problem(w1, u, mask, J, ins, tgs))
     assert abs(F - Fo) <= TOL_F
     assert grad_close(g, go)
+
+
+def test_full_size_operator_form_sampled_overlaps():
+    """The operator form at the gate workload's full size (N=50, chi=20,
+    K=100, its autotuned launch shape) on two noise samples, with an X-gate
+    target near the pi pulse so that the overlaps are O(1): every overlap
+    against the oracle.  (The gradient is checked at smaller sizes: the
+    oracle's costate sweep over 80 x 80 operator thetas takes minutes.)"""
+    from paper_2603_03639_gb300 import autotune
+    w0 = synth.WORKLOADS["cnotgate50"]
+    warps, ctas = autotune.lookup(w0.N, w0.K, w0.chi, w0.M, w0.P, w0.C, grad=True, operator=True)
+    w = w0.replace(M=2, target="x", g_bonds="all")
+    u = synth.pi_pulse_controls(w.K, w.C, w.N, w.dt, seed=7, jitter=0.05)
+    u, mask, J, ins, tgs = case(w, u)
+    ctx = gpu_context(w, ins, tgs, mask, warps=warps, ctas_per_sm=ctas)
+    ctx.set_controls(u)
+    ctx.set_noise(J)
+    F = ctx.fidelity()
+    O = ctx.overlaps()
+    assert F > 0.1
+    pb = oracle_problem(w, u, mask, J, ins, tgs)
+    for s in range(w.M):
+        o, _ = robust.trajectory(pb, s, 0, want_grad=False)
+        assert abs(O[s, 0] - o) <= TOL_O
 
 
 def test_packed_history_and_checkpoint_fallback_agree(monkeypatch):
