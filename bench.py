@@ -315,6 +315,8 @@ def gpu_arm(args, w):
                         dtype=torch.float64, device=dev)
     torch.cuda.synchronize(dev)
     measured_peak = measure_fp64_peak(probe.data_ptr(), probe.numel() * 8) / 1e3
+    from paper_2603_03639_gb300.tnrc import measure_dmma_peak
+    measured_dmma = measure_dmma_peak(probe.data_ptr(), probe.numel() * 8) / 1e3
     achieved = (alg / launches) / (traj_ms / launches / 1000.0) / 1e12 if launches else None
     traffic = recorded_traffic(w.name)
     line = {
@@ -338,6 +340,7 @@ def gpu_arm(args, w):
                      "kernel": "tnrc::traj_kernel",
                      "peak_source": "derived FP64 FMA peak: 2 DFMA/clk/SM x 152 SMs x 2070 MHz",
                      "measured_fp64_fma_peak": measured_peak,
+                     "measured_fp64_dmma_peak": measured_dmma,
                      "frac_of_measured": (achieved / measured_peak) if achieved and measured_peak else None},
         "clocks": clk.summary(),
         "workload_stats": {"alg_flops_per_step": alg / args.steps, "traj_kernel_ms_per_step": traj_ms / args.steps,

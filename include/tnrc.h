@@ -237,6 +237,14 @@ void tnrc_destroy(tnrc_ctx* ctx);
  * arithmetic (the paper has no counterpart; it quotes no hardware). */
 tnrc_status tnrc_measure_fp64_peak(void* scratch, size_t scratch_bytes, double* gflops);
 
+/* Measure the current device's FP64 tensor-core (DMMA, m8n8k4) throughput in
+ * GFLOP/s: 4 independent multiply-accumulate chains per warp on 4 CTAs x 256
+ * threads per SM, best of 4 timed launches after a warm-up, on the legacy
+ * default stream; `scratch` as above.  It tells whether the trajectory
+ * kernel's contractions would gain from the FP64 tensor path (the paper has
+ * no counterpart; it quotes no hardware). */
+tnrc_status tnrc_measure_dmma_peak(void* scratch, size_t scratch_bytes, double* gflops);
+
 /* After TNRC_E_CUDA: which CUDA call failed and why ("" otherwise).  The
  * string lives as long as the context. */
 const char* tnrc_last_error(const tnrc_ctx* ctx);

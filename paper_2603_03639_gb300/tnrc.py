@@ -21,7 +21,8 @@ EXPORTS = ("tnrc_create", "tnrc_set_controls", "tnrc_sample_noise", "tnrc_set_no
            "tnrc_fidelity",
            "tnrc_fidelity_grad", "tnrc_get_overlaps", "tnrc_get_stats", "tnrc_set_controls_dev",
            "tnrc_evaluate_dev", "tnrc_sync", "tnrc_footprint", "tnrc_destroy", "tnrc_status_string",
-           "tnrc_fidelity_static", "tnrc_set_graphs", "tnrc_last_error", "tnrc_measure_fp64_peak")
+           "tnrc_fidelity_static", "tnrc_set_graphs", "tnrc_last_error", "tnrc_measure_fp64_peak",
+           "tnrc_measure_dmma_peak")
 
 
 class TNRCError(RuntimeError):
@@ -84,6 +85,8 @@ def lib() -> ctypes.CDLL:
         L.tnrc_sync.argtypes = [vp]
         L.tnrc_measure_fp64_peak.argtypes = [vp, ctypes.c_size_t, dp]
         L.tnrc_measure_fp64_peak.restype = i32
+        L.tnrc_measure_dmma_peak.argtypes = [vp, ctypes.c_size_t, dp]
+        L.tnrc_measure_dmma_peak.restype = i32
         L.tnrc_last_error.argtypes = [vp]
         L.tnrc_last_error.restype = ctypes.c_char_p
         L.tnrc_set_graphs.argtypes = [vp, i32]
@@ -194,6 +197,14 @@ def measure_fp64_peak(scratch_ptr: int, scratch_bytes: int) -> float:
     g = np.zeros(1)
     _check(lib().tnrc_measure_fp64_peak(ctypes.c_void_p(scratch_ptr), scratch_bytes, _dp(g)),
            "tnrc_measure_fp64_peak")
+    return float(g[0])
+
+
+def measure_dmma_peak(scratch_ptr: int, scratch_bytes: int) -> float:
+    """FP64 tensor-core (DMMA) throughput of the current device in GFLOP/s."""
+    g = np.zeros(1)
+    _check(lib().tnrc_measure_dmma_peak(ctypes.c_void_p(scratch_ptr), scratch_bytes, _dp(g)),
+           "tnrc_measure_dmma_peak")
     return float(g[0])
 
 
