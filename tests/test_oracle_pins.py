@@ -178,6 +178,37 @@ def test_mps_state_matches_dense_vector_elementwise():
         assert np.all(sv[k:] < 1e-12)
 
 
+@pytest.mark.parametrize("chi,eps", [(3, 1e-12), (8, 1e-2), (2, 1e-12)])
+def test_one_truncated_update_is_the_dense_schmidt_projection(chi, eps):
+    """On a state in exact canonical form, one truncated two-site update is the
+    dense rule written out: apply the gate, Schmidt-decompose the vector across
+    the bond, keep k = min(chi, #{sigma_i > max(eps, 1e-13) sigma_1}) values,
+    renormalise.  The kept Schmidt values and the whole state vector must agree
+    (the projection is unique when the cut is not a tie, which is checked)."""
+    N = 7
+    rng = np.random.default_rng(17 + chi)
+    # an entangled canonical state: a random MPS of bond 6
+    sites = []
+    dims = [1, 2, 4, 6, 6, 4, 2, 1]
+    for i in range(N):
+        sites.append(rng.normal(size=(dims[i], 2, dims[i + 1])) + 1j * rng.normal(size=(dims[i], 2, dims[i + 1])))
+    B, lam = mps.canonicalize(sites, 64, 1e-14)
+    psi = mps.to_dense(B)
+    for b in (2, 3):
+        Bb, lamb = [x.copy() for x in B], [x.copy() for x in lam]
+        h = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
+        G = gates.expm_hermitian(h + h.conj().T, 0.7)[0]
+        mps.two_site_update(Bb, lamb, b, G, chi, eps)
+        v = dense.apply_two_site(psi, G, b, N)
+        U, S, Vh = np.linalg.svd(v.reshape(2 ** (b + 1), -1), full_matrices=False)
+        k = max(1, min(chi, int(np.count_nonzero(S > max(eps, 1e-13) * S[0]))))
+        assert S[k - 1] - (S[k] if k < len(S) else 0.0) > 1e-6      # no tie at the cut
+        ref = (U[:, :k] * S[:k]) @ Vh[:k] / np.linalg.norm(S[:k])
+        assert len(lamb[b]) == k
+        assert np.max(np.abs(lamb[b] - S[:k] / np.linalg.norm(S[:k]))) < 1e-12
+        assert np.max(np.abs(mps.to_dense(Bb) - ref.reshape(-1))) < 1e-12
+
+
 # ------------------------------------------------------- Trotter error is O(dt^2)
 def test_second_order_trotter_error_scaling():
     N, K0, T = 4, 2, 1.0
