@@ -429,6 +429,11 @@ def serving_run(probs, rate, n_req, max_inflight, seed):
     st = latency_stats(reqs)
     st["peak_inflight"] = peak
     st["offered_rps"] = rate
+    # per size class (chain length): p50/p99 latency of that class's requests
+    st["by_N"] = {}
+    for n in sorted({r.N for r in reqs}):
+        sub = latency_stats([r for r in reqs if r.N == n])
+        st["by_N"][str(n)] = {k: sub[k] for k in ("n", "p50_s", "p99_s") if k in sub}
     return st, reqs
 
 
