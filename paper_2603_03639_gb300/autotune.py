@@ -93,7 +93,7 @@ def main():
     ap.add_argument("--set", action="append", default=[], metavar="KEY=VALUE")
     ap.add_argument("--out", default=DEFAULT_CACHE)
     ap.add_argument("--fidelity-only", action="store_true")
-    ap.add_argument("--quick", action="store_true", help="only the four usual winners")
+    ap.add_argument("--quick", action="store_true", help="only the usual winners (QUICK)")
     args = ap.parse_args()
     w = synth.WORKLOADS[args.workload]
     for kv in args.set:
