@@ -168,8 +168,12 @@ tnrc_status tnrc_get_noise(tnrc_ctx* ctx, double* J, int64_t len);
  * Errors: TNRC_E_STATE if controls or noise are missing. */
 tnrc_status tnrc_fidelity(tnrc_ctx* ctx, double* F, double* per_traj);
 
-/* F and grad[K][C][N] = dF/du (host), with the forward states checkpointed every
- * checkpoint_every slices and recomputed in the costate sweep (App. A). */
+/* F and grad[K][C][N] = dF/du (host) by the costate sweep (App. A).  The forward
+ * layer states are kept packed at their actual bond dimensions for the sweep;
+ * a trajectory whose history does not fit its CTA's region is redone with
+ * checkpoints every checkpoint_every slices and recomputation (same results).
+ * Errors: TNRC_E_STATE if controls or noise are missing; TNRC_E_NUMERIC if the
+ * SVD did not converge or a non-finite value appeared. */
 tnrc_status tnrc_fidelity_grad(tnrc_ctx* ctx, double* F, double* grad);
 
 /* Overlaps O[M][P] (host, interleaved complex128) of the last evaluation. */
