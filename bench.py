@@ -15,6 +15,7 @@ own shard of noise samples).
 bounded sample of the same workload.  --plain compares one CTA (one
 trajectory at a time) with the persistent launch on a sample; --serving runs
 the serving rate sweep; --workload picks another shape (x8, x50, ghz30, the
+near-solution cnot50near, echo14 whose bonds reach the cap chi = 64, the
 operator-form cnotgate50); --set KEY=VALUE overrides a field (profiling cases).
 """
 import argparse
@@ -56,13 +57,16 @@ def form_kwargs(w):
 
 def workload_config(w):
     kind = {"x": "parallel X", "cnot": "parallel CNOT", "ghz": "GHZ preparation",
-            "heisenberg": "Heisenberg ground state"}[w.target]
+            "heisenberg": "Heisenberg ground state", "input": "echo back to the input"}[w.target]
     if w.operator:
         kind += " gate (MPO from the identity, |tr(U_T^dag U)/2^N|^2)"
-    cfg = {"workload": "%s: %s on N=%d, chi_max=%d, K=%d, dt=%g, C=%d, M=%d, P=%d, %s J, controls N(0,%g^2)"
+    ctl = {"random": "controls N(0,%g^2)" % w.u_sigma,
+           "near": "near-solution controls (pi pulse + N(0,0.05^2))",
+           "echo": "echo controls (N(0,%g^2), then reversed and negated)" % w.u_sigma}[w.u_mode]
+    cfg = {"workload": "%s: %s on N=%d, chi_max=%d, K=%d, dt=%g, C=%d, M=%d, P=%d, %s J, %s"
                        % (w.name, kind, w.N, w.chi, w.K, w.dt, w.C, w.M, w.P,
                           ("U[-%g,%g]" % (w.noise_scale, w.noise_scale)) if w.noise_dist == 0
-                          else ("N(0,%g^2)" % w.noise_scale), w.u_sigma),
+                          else ("N(0,%g^2)" % w.noise_scale), ctl),
            "N": w.N, "chi_max": w.chi, "K": w.K, "M": w.M, "P": w.P, "C": w.C, "dt": w.dt,
            "slice_steps_per_eval": w.slice_steps}
     if w.order != 2 or w.substeps != 1 or w.crosstalk != 1 or w.operator:
@@ -148,9 +152,13 @@ def oracle_sample(w, n_traj, K_s, workers):
 def cpu_baseline(w, budget_steps=1):
     workers = os.cpu_count() or 1
     units, secs, used = oracle_sample(w, workers, w.K, workers)
+    u1, s1, _ = oracle_sample(w, 1, w.K, 1)
     return {"value": units / secs, "unit": UNIT, "cores": used, "kind": "oracle",
             "sample": "%d trajectories (noise samples 0..%d, input 0) x all %d slices, fwd+adjoint, "
-                      "one per spawn worker, OMP/BLAS 1 thread each: %.1f s" % (used, used - 1, w.K, secs)}
+                      "one per spawn worker, OMP/BLAS 1 thread each: %.1f s" % (used, used - 1, w.K, secs),
+            "single_core": {"value": u1 / s1, "unit": UNIT, "cores": 1,
+                            "sample": "1 trajectory (noise sample 0, input 0) x all %d slices, fwd+adjoint, "
+                                      "one spawn worker, BLAS 1 thread: %.1f s" % (w.K, s1)}}
 
 
 def reference_arm(args, w):
@@ -256,7 +264,7 @@ def gpu_arm(args, w):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     per_step, alg, traj_ms, launches = [], 0.0, 0.0, 0
     hist = np.zeros(w.chi + 1, dtype=np.int64)
-    disc, sweeps, updates, maxb = 0.0, 0, 0, 0
+    disc, sweeps, updates, maxb, capcuts, mingap = 0.0, 0, 0, 0, 0, None
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -278,6 +286,9 @@ def gpu_arm(args, w):
             sweeps += st["jacobi_sweeps"]
             updates += st["updates"]
             maxb = max(maxb, st["max_bond"])
+            capcuts += st["cap_truncations"]
+            if st["min_trunc_gap"] >= 0.0:
+                mingap = st["min_trunc_gap"] if mingap is None else min(mingap, st["min_trunc_gap"])
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
@@ -346,7 +357,12 @@ def gpu_arm(args, w):
         "workload_stats": {"alg_flops_per_step": alg / args.steps, "traj_kernel_ms_per_step": traj_ms / args.steps,
                            "max_bond": maxb, "bond_hist": hist.tolist(), "discarded_weight": disc / args.steps,
                            "jacobi_sweeps_per_update": sweeps / max(1, updates),
-                           "updates_per_step": updates / args.steps},
+                           "updates_per_step": updates / args.steps,
+                           # cuts the cap chi_max decided (more values above the cutoff than it
+                           # keeps) and their smallest (sigma_k - sigma_k+1) / sigma_1; below
+                           # 1e-10 a cut is a tie
+                           "cap_truncations_per_step": capcuts / args.steps, "min_trunc_gap": mingap,
+                           "tie_at_cut": bool(mingap is not None and mingap < 1e-10)},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)

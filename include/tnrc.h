@@ -137,6 +137,15 @@ typedef struct {
                                     kernel (contraction, Jacobi, rank/truncate, split,
                                     environments, gradients, history copies, layer
                                     barriers); zero unless built with TNRC_PHASE_TIMERS   */
+  int64_t cap_truncations;       /* truncations of the last evaluation (forward and costate
+                                    updates) whose cut the cap decided: more singular values
+                                    exceeded the cutoff than chi_max keeps (Sec. II, D_max)  */
+  double min_trunc_gap;          /* smallest (sigma_k - sigma_{k+1}) / sigma_1 over those cuts,
+                                    k = chi_max: the relative distance between the last kept
+                                    and the first dropped singular value.  Below 1e-10 the cut
+                                    is a tie (the kept subspace is then decided by rounding,
+                                    and two correct implementations may differ there); -1
+                                    when the cap decided no cut                             */
 } tnrc_stats;
 
 /* Create a context on the current CUDA device, ordered on `cuda_stream`
@@ -221,8 +230,13 @@ tnrc_status tnrc_sync(tnrc_ctx* ctx);
  * do not fit the 32 MiB array or an input bond dimension exceeds 64.  The
  * array is shared by every call and keeps the last call's contents (each call
  * clears what must start at zero); calls whose device work overlaps race on
- * it and must be serialised.  The first call on a device looks up the
- * array's device address; make it before any stream capture. */
+ * it and must be serialised.  Every call looks up the array's device address
+ * on the current device and synchronises its stream before returning.  With
+ * CUDA's lazy module loading (the default) the array is placed on a device at
+ * the first call there (or at library load with CUDA_MODULE_LOADING=EAGER), so
+ * a caller that must not grow its device footprint later makes one small
+ * call at start-up; after that, calls allocate nothing.  Problems are
+ * validated by the same rules as tnrc_create (TNRC_E_INVALID). */
 tnrc_status tnrc_fidelity_static(const tnrc_problem* problem, const tnrc_mps* inputs,
                                  const tnrc_mps* targets, const double* u, const double* J,
                                  void* cuda_stream, double* F, double* per_traj);

@@ -61,14 +61,20 @@ def canonicalize(sites, chi, eps):
     return B, lam
 
 
-def two_site_update(B, lam, b, G, chi, eps):
+def two_site_update(B, lam, b, G, chi, eps, info=None):
     """Apply the d^2 x d^2 gate G (basis |s_b s_{b+1}>) on bond b and truncate.
 
     theta = lam_{b-1} . G (B_b B_{b+1}) reshaped (d D_l) x (d D_r);
     theta = X S Y^dagger;  keep k values;  B_{b+1} <- Y_k^dagger,
     B_b <- Phi Y_k / ||S_k|| with Phi = G (B_b B_{b+1}) (no division by lam),
     lam_b <- S_k / ||S_k||.  Returns the discarded weight
-    sum_{i>k} sigma_i^2 / sum_i sigma_i^2."""
+    sum_{i>k} sigma_i^2 / sum_i sigma_i^2 and k.
+
+    Diagnostic only: when ``info`` (a dict) is given, info["gap"] receives
+    (sigma_k - sigma_{k+1}) / sigma_1 if the cap chi (not the cutoff) decided
+    the cut -- more than chi values above the cutoff -- else None.  A gap near
+    zero is a tie at the cut: the kept subspace is then not fixed by the
+    singular values, and rounding decides it."""
     A, C = B[b], B[b + 1]
     dl, d, dr = A.shape[0], A.shape[1], C.shape[2]
     lam_l = lam[b - 1] if b > 0 else np.ones(1)
@@ -78,6 +84,9 @@ def two_site_update(B, lam, b, G, chi, eps):
     theta = lam_l[:, None, None, None] * Phi
     U, S, Vh = np.linalg.svd(theta.reshape(dl * d, d * dr), full_matrices=False)
     k = _keep(S, chi, eps)
+    if info is not None:
+        above = int(np.count_nonzero(S > max(eps, ZERO_FLOOR) * S[0]))
+        info["gap"] = float((S[k - 1] - S[k]) / S[0]) if above > k else None
     nrm = np.linalg.norm(S[:k])
     Yk = Vh[:k].conj().T
     B[b + 1] = Vh[:k].reshape(k, d, dr)

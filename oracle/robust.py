@@ -222,8 +222,21 @@ def _layer_bonds(N, parity):
     return list(range(parity, N - 1, 2))
 
 
+def _note_cut(stats, info):
+    """Record a cap-decided cut in ``stats`` (diagnostic: "cap_cuts", "min_gap")."""
+    if stats is not None and info.get("gap") is not None:
+        stats["cap_cuts"] = stats.get("cap_cuts", 0) + 1
+        stats["min_gap"] = min(stats.get("min_gap", np.inf), info["gap"])
+
+
 def trajectory(pb: Problem, s: int, p: int, want_grad: bool = True, stats=None):
-    """(O_sp, dO_sp[K][C][N] or None) for noise sample s and input p."""
+    """(O_sp, dO_sp[K][C][N] or None) for noise sample s and input p.
+
+    ``stats`` (a dict, optional) collects diagnostics: "discarded" (forward
+    discarded weight), "dims" (forward bond dimensions), and over the forward
+    and costate updates "cap_cuts" (cuts the cap chi decided) and "min_gap"
+    (smallest relative gap at such a cut, see ``mps.two_site_update``)."""
+    info = {}
     N = pb.N
     B, lam = _m.canonicalize(pb.inputs[p], pb.chi, pb.eps)
     T, tlam = _m.canonicalize(pb.targets[p], pb.chi, pb.eps)
@@ -241,10 +254,11 @@ def trajectory(pb: Problem, s: int, p: int, want_grad: bool = True, stats=None):
             if pb.operator:
                 Mg = embed_out(Mg)
             gl[b] = (Mg, parts)
-            w, kk = _m.two_site_update(B, lam, b, Mg, pb.chi, pb.eps)
+            w, kk = _m.two_site_update(B, lam, b, Mg, pb.chi, pb.eps, info)
             if stats is not None:
                 stats["discarded"] += w
                 stats["dims"].append(kk)
+                _note_cut(stats, info)
         gate_cache.append(gl)
         if want_grad:
             hist.append(([x.copy() for x in B], [x.copy() for x in lam]))
@@ -272,7 +286,8 @@ def trajectory(pb: Problem, s: int, p: int, want_grad: bool = True, stats=None):
                 Lt = Lt @ G
         for b in _layer_bonds(N, par):
             Mg = gate_cache[li][b][0]
-            _m.two_site_update(cB, clam, b, Mg.conj().T, pb.chi, pb.eps)
+            _m.two_site_update(cB, clam, b, Mg.conj().T, pb.chi, pb.eps, info)
+            _note_cut(stats, info)
     return O, dO
 
 

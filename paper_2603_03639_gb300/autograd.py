@@ -4,15 +4,20 @@
 a differentiable scalar of the control tensor u[K][C][N] (CUDA, float64).
 Its backward is the hand-written costate (adjoint) kernel of App. A: the
 trajectory kernel propagates the target backwards through the truncated
-layers, recomputing the forward states segment by segment from checkpoints
-taken every ``checkpoint_every`` slices (ceil(sqrt(K)) by default), so the
-device memory per trajectory stays at about (K/s + 3s + 2) MPS.
+layers.  The forward layer states it needs are read from a packed history
+written during the forward pass at their actual bond dimensions (the default:
+nothing is recomputed).  Each CTA's work region is sized for about
+2 sqrt(L) full-capacity MPS (L truncated layers); a trajectory whose packed
+history outgrows it is redone on the fallback path, which keeps checkpoints
+every ``checkpoint_every`` slices (about sqrt(L) layers by default) and
+recomputes each segment, so device memory stays bounded by the sqrt-sized
+region either way (results are bitwise the same on both paths).
 
 When the graph requires a gradient, the adjoint runs in the same device
-launch as the forward pass (one forward, one recomputation and one costate
-sweep per trajectory, instead of a second forward in a separate backward
-launch) and its result dF/du is held until ``backward``; otherwise only the
-forward pass runs.  Everything is stream-ordered on the context's stream;
+launch as the forward pass (one forward and one costate sweep per
+trajectory, instead of a second forward in a separate backward launch) and
+its result dF/du is held until ``backward``; otherwise only the forward pass
+runs.  Everything is stream-ordered on the context's stream;
 no host synchronisation happens in either direction.
 """
 import torch

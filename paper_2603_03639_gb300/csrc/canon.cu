@@ -57,7 +57,8 @@ __global__ void canon_kernel(CanonArgs a) {
     fro = warp_sum(fro);
     __syncwarp();
     const int sw = warp_jacobi(T, n, m, fro, cn, lane);
-    int r = warp_rank_truncate(T, n, m, m, a.eps, sig2, perm, lane, kept2, tot2);
+    double gap;
+    int r = warp_rank_truncate(T, n, m, m, a.eps, sig2, perm, lane, kept2, tot2, gap);
     if (r > n) r = n;
     if (lane == 0 && sw < 0) atomicOr(a.status, kStatusNoConverge);
     // U_r into site i
@@ -123,7 +124,8 @@ __global__ void canon_kernel(CanonArgs a) {
     fro = warp_sum(fro);
     __syncwarp();
     const int sw = warp_jacobi(T, n, m, fro, cn, lane);
-    int k = warp_rank_truncate(T, n, m, a.chi, a.eps, sig2, perm, lane, kept2, tot2);
+    double gap;
+    int k = warp_rank_truncate(T, n, m, a.chi, a.eps, sig2, perm, lane, kept2, tot2, gap);
     if (k > n) k = n;
     if (lane == 0 && sw < 0) atomicOr(a.status, kStatusNoConverge);
     const double inv_kn = rsqrt(kept2);

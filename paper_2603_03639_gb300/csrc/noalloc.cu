@@ -14,23 +14,27 @@
 // The array is shared by all calls: each call overwrites it and clears the
 // parts that must start at zero.  Calls whose device work overlaps (two host
 // threads, or two streams, at the same time) race on it; serialise them.
-// The first call on a device looks up the array's device address (once per
-// device, under a lock, with that device current); make that first call
-// before any stream capture.
+// Every call looks up the array's device address on the current device
+// (cudaGetSymbolAddress, checked), so the address stays right after a device
+// reset; the call synchronises its stream, so it is never stream-captured.
+// With CUDA's lazy module loading (the default) the array is placed on a
+// device at the first call there -- that call grows the device footprint by
+// kStaticBytes -- or when the library loads, with CUDA_MODULE_LOADING=EAGER;
+// callers that must not grow their footprint later make one small call at
+// start-up.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <vector>
 
 #include "../../include/tnrc.h"
+#include "plan.h"
 #include "tnrc_device.cuh"
 
 extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, size_t smem, cudaStream_t st);
 extern "C" cudaError_t tnrc_traj_prepare();
-extern "C" size_t tnrc_traj_smem(int warps, int slab_elems);
 extern "C" cudaError_t tnrc_launch_layer_gates(int N, int K, int C, int M, int terms, int order, int nsub,
                                                int L, int R, int first_parity, double dt, const double* u,
                                                const unsigned char* mask, const double* gfix, const double* J,
@@ -43,28 +47,17 @@ extern "C" cudaError_t tnrc_launch_canon(const tnrc::CanonArgs* a, int nmps, cud
 namespace {
 
 constexpr size_t kStaticBytes = size_t(32) << 20;   // 32 MiB per device
-constexpr int kMaxDevices = 64;
 constexpr int kMaxInputDimStatic = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {nullptr};
-
-// Device address of g_static_scratch on the current device (looked up once).
+// Device address of g_static_scratch on the current device.  Host code
+// cannot use the array's name as a device address; the runtime maps it.
 cudaError_t static_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
+  *out = p;
   return cudaSuccess;
 }
 
@@ -75,41 +68,25 @@ int64_t up(int64_t x) { return (x + 255) / 256 * 256; }
 extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_mps* inputs,
                                             const tnrc_mps* targets, const double* u, const double* J,
                                             void* cuda_stream, double* F, double* per_traj) {
-  // ---- validation (host only) ----
+  // ---- validation (host only; the same rules as tnrc_create) ----
   if (!pb || !inputs || !targets || !u || !J || !F || pb->struct_size != sizeof(tnrc_problem))
     return TNRC_E_INVALID;
-  const int N = pb->n_sites, K = pb->n_slices, chi = pb->chi_max, M = pb->n_samples, P = pb->n_inputs,
-            C = pb->n_controls;
-  if (N < 2 || N > 256 || K < 1 || chi < 1 || chi > tnrc::kMaxChi || M < 1 || P < 1 || (C != 2 && C != 3))
-    return TNRC_E_INVALID;
-  if (pb->crosstalk_terms != 0 && pb->crosstalk_terms != 1 && pb->crosstalk_terms != 3) return TNRC_E_INVALID;
-  const int terms = pb->crosstalk_terms == 3 ? 3 : 1;
-  if (pb->trotter_order < 0 || pb->trotter_order > 2 || pb->substeps < 0) return TNRC_E_INVALID;
-  const int order = pb->trotter_order == 1 ? 1 : 2;
-  if (pb->operator_form != 0 && pb->operator_form != 1) return TNRC_E_INVALID;
-  const int d = pb->operator_form ? 4 : 2;   // physical dimension
-  const int lg = pb->operator_form ? 2 : 1;  // log2 d
-  if (d * chi > tnrc::kMaxDim) return TNRC_E_INVALID;
-  const int nsub = pb->substeps > 0 ? pb->substeps : 1;
-  if ((long long)K * nsub > (1 << 20)) return TNRC_E_INVALID;
-  // truncated layers (alternating bond parity) and their gate records per sample
-  const int S = K * nsub;
-  const int n_layers = (order == 2) ? 2 * S + 1 : 2 * S;
-  const int first_parity = (order == 2) ? 0 : 1;
-  std::vector<int> layer_off(n_layers + 1, 0);
-  for (int l = 0; l < n_layers; ++l) layer_off[l + 1] = layer_off[l] + (N - 1 - ((l + first_parity) & 1) + 1) / 2;
-  const int recs = layer_off[n_layers];
-  if (!(pb->dt > 0.0) || !std::isfinite(pb->dt) || !(pb->sv_cutoff >= 0.0) || !(pb->sv_cutoff < 1.0))
-    return TNRC_E_INVALID;
+  tnrc_host::Plan plan;
+  if (!tnrc_host::make_plan(pb, 1, 0, plan, false)) return TNRC_E_INVALID;
+  if (tnrc_host::check_problem_arrays(pb, inputs, targets) != TNRC_OK) return TNRC_E_INVALID;
+  const int N = plan.N, K = plan.K, chi = plan.chi, M = plan.M, P = plan.P, C = plan.C;
+  const int terms = plan.terms, order = plan.order, nsub = plan.nsub, d = plan.d;
+  const int n_layers = plan.n_layers, first_parity = plan.first_parity, recs = plan.recs;
+  const std::vector<int>& layer_off = plan.layer_off;
+  const std::vector<int>& dcap = plan.dcap;
+  const std::vector<int>& site_off = plan.site_off;
+  const tnrc::SlotLayout L = plan.L;
   const long long T = (long long)M * P;
   if (T > (1 << 24)) return TNRC_E_TOO_LARGE;
   int dmax = chi;
   for (int j = 0; j < 2 * P; ++j) {
     const tnrc_mps& m = (j < P) ? inputs[j] : targets[j - P];
-    if (m.n_sites != N || !m.bond_dims || !m.data || m.bond_dims[0] != 1 || m.bond_dims[N] != 1)
-      return TNRC_E_INVALID;
     for (int i = 0; i <= N; ++i) {
-      if (m.bond_dims[i] < 1) return TNRC_E_INVALID;
       if (m.bond_dims[i] > kMaxInputDimStatic) return TNRC_E_TOO_LARGE;
       dmax = std::max(dmax, m.bond_dims[i]);
     }
@@ -119,26 +96,6 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
     if (!std::isfinite(u[i])) return TNRC_E_INVALID;
   for (int64_t i = 0; i < (int64_t)M * (N - 1) * terms; ++i)
     if (!std::isfinite(J[i])) return TNRC_E_INVALID;
-
-  // ---- layout of one state slot (capacity D_i = min(2^i, 2^(N-i), chi)) ----
-  std::vector<int> dcap(N + 1, 1), site_off(N);
-  for (int i = 1; i < N; ++i) {
-    const int a = i * lg >= 30 ? chi : std::min(1 << (i * lg), chi);
-    const int b = (N - i) * lg >= 30 ? chi : std::min(1 << ((N - i) * lg), chi);
-    dcap[i] = std::min(a, b);
-  }
-  int64_t elems = 0;
-  for (int i = 0; i < N; ++i) {
-    site_off[i] = (int)elems;
-    elems += (int64_t)dcap[i] * d * dcap[i + 1];
-    elems = (elems + 1) / 2 * 2;
-  }
-  tnrc::SlotLayout L;
-  L.N = N;
-  L.chi = chi;
-  L.lam_off = ((int64_t)(N + 1) * 4 + 15) / 16 * 16;
-  L.sites_off = up(L.lam_off + (int64_t)(N - 1) * chi * 8);
-  L.bytes = up(L.sites_off + elems * 16);
 
   // ---- static scratch map ----
   std::vector<int> rdims((size_t)2 * P * (N + 1));
@@ -190,15 +147,7 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   cudaStream_t st = (cudaStream_t)cuda_stream;
 
   // ---- stage inputs ----
-  std::vector<unsigned char> mask((size_t)C * N, 1);
-  if (pb->control_mask) {
-    for (int i = 0; i < C * N; ++i)
-      if (pb->control_mask[i] > 1) return TNRC_E_INVALID;
-    std::memcpy(mask.data(), pb->control_mask, mask.size());
-  } else if (C == 3) {
-    for (int i = 0; i < N; ++i) mask[2 * N + i] = (i < N - 1) ? 1 : 0;
-  }
-  if (C == 3) mask[2 * N + N - 1] = 0;
+  const std::vector<unsigned char> mask = tnrc_host::control_mask(pb);
   std::vector<double> gfix((size_t)K * (N - 1), 0.0);
   if (pb->g_fixed) std::memcpy(gfix.data(), pb->g_fixed, gfix.size() * 8);
   std::vector<double> raw((size_t)rtotal * 2);

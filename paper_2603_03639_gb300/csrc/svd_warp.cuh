@@ -264,12 +264,15 @@ __device__ inline int warp_qrcp(double2* W, int m, int n, double thr, int* piv, 
 }
 
 // Column norms, ranking and the truncation decision after warp_jacobi.
-// sig2[j] = |column j|^2 (j < m); perm[i] = column of rank i (i < k), ranks by
-// decreasing sigma with ties broken by the smaller index.  Returns k =
-// max(1, min(kcap, #{sigma_j > eps sigma_max})); kept2 / tot2 receive the
-// squared norms of the kept values and of all values.
+// sig2[j] = |column j|^2 (j < m); perm[i] = column of rank i (i <= k, i < m),
+// ranks by decreasing sigma with ties broken by the smaller index.  Returns
+// k = max(1, min(kcap, #{sigma_j > eps sigma_max})); kept2 / tot2 receive the
+// squared norms of the kept values and of all values.  When the cap decided
+// the cut (more than kcap values above the cutoff), gap = (sigma_(k) -
+// sigma_(k+1)) / sigma_max, the relative distance between the last kept and
+// the first dropped value; otherwise gap = -1.
 __device__ inline int warp_rank_truncate(const double2* T, int n, int m, int kcap, double eps, double* sig2,
-                                  int* perm, int lane, double& kept2, double& tot2) {
+                                  int* perm, int lane, double& kept2, double& tot2, double& gap) {
   for (int j = lane; j < m; j += 32) {
     const double2* c = T + (size_t)j * n;
     double s = 0.0;
@@ -298,13 +301,14 @@ __device__ inline int warp_rank_truncate(const double2* T, int n, int m, int kca
       const long long vi = __double_as_longlong(sig2[i]);
       rk += (vi > vj || (vi == vj && i < j)) ? 1 : 0;
     }
-    if (rk < k) perm[rk] = j;
+    if (rk <= k) perm[rk] = j;
   }
   __syncwarp();
   double kn = 0.0;
   for (int i = lane; i < k; i += 32) kn += sig2[perm[i]];
   kept2 = warp_sum(kn);
   tot2 = tot;
+  gap = (cnt > k && k < m) ? (sqrt(sig2[perm[k - 1]]) - sqrt(sig2[perm[k]])) / sqrt(mx) : -1.0;
   return k;
 }
 

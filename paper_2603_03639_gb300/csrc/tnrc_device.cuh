@@ -27,7 +27,10 @@ constexpr int kStatusNaN = 2;
 constexpr int kStatusBadDims = 4;
 constexpr int kCtrPhase = 5 + kMaxChi + 1;      // first of kNumPhases cycle counters
 constexpr int kNumPhases = 8;
-constexpr int kNumCounters = kCtrPhase + kNumPhases;   // device counters of one evaluation
+constexpr int kCtrCapTrunc = kCtrPhase + kNumPhases;  // truncations whose cut the cap chi_max decided
+constexpr int kCtrGap = kCtrCapTrunc + 1;              // smallest relative gap at such a cut (double bits;
+                                                       // starts as all ones, lowered by atomicMin)
+constexpr int kNumCounters = kCtrGap + 1;              // device counters of one evaluation
 
 // Per-phase cycle counters (lane 0 of every warp, clock64), compiled in only
 // with -DTNRC_PHASE_TIMERS: 0 contraction, 1 Jacobi sweeps, 2 rank/truncate,

@@ -44,6 +44,7 @@ struct WarpCtx {
   double disc;
   int maxk;
   unsigned long long alg;   // algorithmic flops counted by lane 0
+  long long capcuts;        // cuts decided by the cap chi (forward and costate updates)
   long long ph[kNumPhases]; // phase cycles (TNRC_PHASE_TIMERS builds)
   int* order;               // shared, CTA-wide: bonds of the current layer by decreasing cost
   int* next;                // shared, CTA-wide: next entry of `order` to take
@@ -160,8 +161,8 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
 
   // Phase 3: rank, truncate.
   TNRC_TIC(t_r);
-  double kept2, tot2;
-  int k = warp_rank_truncate(T, n, r, chi, p.eps, w.sig2, w.perm, lane, kept2, tot2);
+  double kept2, tot2, gap;
+  int k = warp_rank_truncate(T, n, r, chi, p.eps, w.sig2, w.perm, lane, kept2, tot2, gap);
   if (k > Y.dcap[b + 1]) {  // cannot happen (k <= min(m, n, chi)); keeps memory in bounds regardless
     k = Y.dcap[b + 1];
     if (lane == 0) atomicOr(p.status, kStatusBadDims);
@@ -177,7 +178,13 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
     if (k > w.maxk) w.maxk = k;
     if (lane == 0) atomicAdd(&p.counters[kCtrHist + k], 1ull);
   }
-  if (count) w.alg += update_flops(m, n, Dc, k);
+  if (count) {
+    w.alg += update_flops(m, n, Dc, k);
+    if (gap >= 0.0) {   // the cap chi_max decided this cut
+      w.capcuts += 1;
+      if (lane == 0) atomicMin(&p.counters[kCtrGap], (unsigned long long)__double_as_longlong(gap));
+    }
+  }
   const double inv_kn = rsqrt(kept2);
   TNRC_TOC(w, 2, t_r);
 
@@ -698,6 +705,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) traj_kernel(TrajParam
   w.sweeps = 0;
   w.updates = 0;
   w.alg = 0;
+  w.capcuts = 0;
   for (int i = 0; i < kNumPhases; ++i) w.ph[i] = 0;
   w.order = s_order;
   w.next = &s_next;
@@ -712,13 +720,14 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) traj_kernel(TrajParam
     const int s = t / p.P, pi = t - s * p.P;
     bool redo = true;
     if (p.want_grad && p.packed_history) {
-      const long long sw0 = w.sweeps, up0 = w.updates;
+      const long long sw0 = w.sweeps, up0 = w.updates, cc0 = w.capcuts;
       const unsigned long long al0 = w.alg;
       redo = run_trajectory<kD>(p, true, base, t, s, pi, w, warp, s_disc, s_maxk, &s_O) != 0;
       if (redo) {  // history outgrew the region: discard the attempt's counts, count the fallback
         w.sweeps = sw0;
         w.updates = up0;
         w.alg = al0;
+        w.capcuts = cc0;
         if (threadIdx.x == 0) atomicAdd(&p.counters[4], 1ull);
       }
     }
@@ -728,6 +737,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) traj_kernel(TrajParam
     atomicAdd(&p.counters[0], (unsigned long long)w.updates);
     atomicAdd(&p.counters[1], (unsigned long long)w.sweeps);
     atomicAdd(&p.counters[3], w.alg);
+    atomicAdd(&p.counters[kCtrCapTrunc], (unsigned long long)w.capcuts);
 #ifdef TNRC_PHASE_TIMERS
     for (int i = 0; i < kNumPhases; ++i) atomicAdd(&p.counters[kCtrPhase + i], (unsigned long long)w.ph[i]);
 #endif

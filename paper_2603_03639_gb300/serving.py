@@ -175,6 +175,15 @@ class Server:
         self.slots = []
 
     # ---- server side ----
+    def _drop(self, slot):
+        """Release a failed slot's context now (its device memory stops
+        counting towards the budget at the same moment)."""
+        try:
+            slot.close()
+        except Exception:
+            pass
+        self.slots.remove(slot)
+
     def _held(self):
         return sum(s.bytes for s in self.slots)
 
@@ -222,7 +231,7 @@ class Server:
                         except Exception as e:  # the context is unusable: drop it, fail the request
                             req.error = "evaluation failed: %s" % e
                             s.busy = None
-                            self.slots.remove(s)
+                            self._drop(s)
                         req.finish = time.perf_counter()
                         s.last_used = req.finish
                         self.done.append(req)
@@ -238,7 +247,7 @@ class Server:
                         self.done.append(req)
                         for s in [s for s in self.slots if s.busy is req]:
                             s.busy = None
-                            self.slots.remove(s)
+                            self._drop(s)
                         admitted = True
                     if not admitted:
                         break

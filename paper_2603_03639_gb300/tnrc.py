@@ -52,7 +52,8 @@ class Stats(ctypes.Structure):
                 ("hist_len", ctypes.c_int32), ("bond_hist", ctypes.c_int64 * 65),
                 ("discarded_weight", ctypes.c_double), ("last_ms", ctypes.c_double),
                 ("alg_flops", ctypes.c_double), ("traj_ms", ctypes.c_double), ("traj_launches", ctypes.c_int64),
-                ("restarts", ctypes.c_int64), ("phase_cycles", ctypes.c_int64 * 8)]
+                ("restarts", ctypes.c_int64), ("phase_cycles", ctypes.c_int64 * 8),
+                ("cap_truncations", ctypes.c_int64), ("min_trunc_gap", ctypes.c_double)]
 
 
 #: trajectory-kernel phases of tnrc_stats.phase_cycles
@@ -315,4 +316,5 @@ class Context:
                 "bond_hist": [int(s.bond_hist[i]) for i in range(s.hist_len)],
                 "discarded_weight": s.discarded_weight, "last_ms": s.last_ms, "alg_flops": s.alg_flops,
                 "traj_ms": s.traj_ms, "traj_launches": s.traj_launches, "restarts": s.restarts,
-                "phase_cycles": dict(zip(PHASES, (int(x) for x in s.phase_cycles)))}
+                "phase_cycles": dict(zip(PHASES, (int(x) for x in s.phase_cycles))),
+                "cap_truncations": int(s.cap_truncations), "min_trunc_gap": float(s.min_trunc_gap)}

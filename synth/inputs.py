@@ -24,7 +24,7 @@ import numpy as np
 __all__ = [
     "MPS", "Workload", "WORKLOADS", "controls", "pi_pulse_controls",
     "product_inputs", "zero_state", "x_targets", "cnot_targets", "ghz_mps",
-    "heisenberg_ground_mps", "control_mask", "make_problem", "identity_operator", "x_gate_operator",
+    "heisenberg_ground_mps", "control_mask", "echo_controls", "make_problem", "identity_operator", "x_gate_operator",
     "cnot_gate_operator",
 ]
 
@@ -89,6 +89,19 @@ def pi_pulse_controls(K: int, C: int, N: int, dt: float, seed: Optional[int] = N
         rng = np.random.default_rng(seed)
         u += rng.normal(0.0, jitter, size=u.shape)
     return u
+
+
+def echo_controls(K: int, C: int, N: int, seed: int, sigma: float) -> np.ndarray:
+    """u[k] ~ N(0, sigma^2) for k < K/2 and u[K-1-k] = -u[k] for the second
+    half (K even): a time-reversed, negated copy.  At zero crosstalk the
+    symmetric splitting then undoes the first half exactly, so the state
+    entangles up to mid-time and disentangles again; the middle bonds can
+    reach the cap while the final overlap with the input stays O(1)."""
+    if K % 2:
+        raise ValueError("echo controls need an even number of slices")
+    rng = np.random.default_rng(seed)
+    h = rng.normal(0.0, sigma, size=(K // 2, C, N))
+    return np.concatenate([h, -h[::-1]]).astype(np.float64)
 
 
 def control_mask(C: int, N: int, g_bonds: str = "none") -> np.ndarray:
@@ -303,7 +316,7 @@ class Workload:
     seed_u: int
     seed_J: int
     seed_in: int
-    target: str              # "x", "cnot", "ghz", "heisenberg"
+    target: str              # "x", "cnot", "ghz", "heisenberg", "input" (target = input)
     g_bonds: str = "none"
     sv_cutoff: float = 1e-12
     u_sigma: float = 0.5
@@ -312,6 +325,11 @@ class Workload:
     substeps: int = 1        # Trotter steps per control bin
     operator: bool = False   # evolve the operator U (MPO, d = 4) from the identity;
                              # F = |tr(U_T^dag U) / 2^N|^2 (Eq. gateinfid)
+    u_mode: str = "random"   # "random": u ~ N(0, u_sigma^2); "near": the pi pulse plus
+                             # N(0, 0.05^2) (the near-solution controls); "echo": the first
+                             # half N(0, u_sigma^2), the second half the first reversed in
+                             # time and negated, so that at zero crosstalk the evolution
+                             # returns to its input (pair with target "input")
 
     @property
     def trajectories(self) -> int:
@@ -323,6 +341,12 @@ class Workload:
         return self.M * self.P * self.K
 
     def controls(self) -> np.ndarray:
+        if self.u_mode == "near":
+            return pi_pulse_controls(self.K, self.C, self.N, self.dt, seed=self.seed_u, jitter=0.05)
+        if self.u_mode == "echo":
+            return echo_controls(self.K, self.C, self.N, self.seed_u, self.u_sigma)
+        if self.u_mode != "random":
+            raise ValueError(self.u_mode)
         return controls(self.K, self.C, self.N, self.seed_u, self.u_sigma)
 
     def mask(self) -> np.ndarray:
@@ -347,14 +371,18 @@ class Workload:
         if self.target == "heisenberg":
             t, _, _ = heisenberg_ground_mps(self.N, min(20, self.chi))
             return [zero_state(self.N)] * self.P, [t] * self.P
+        if self.target == "input":
+            ins = [zero_state(self.N)] + product_inputs(self.N, self.P - 1, self.seed_in)
+            return ins, [m.copy() for m in ins]
         raise ValueError(self.target)
 
     def replace(self, **kw) -> "Workload":
         return dataclasses.replace(self, **kw)
 
 
-#: The five workload shapes: parallel X on 8 and 50 qubits, parallel CNOT on
-#: 50, GHZ on 30 (Sec. III-IV).  "serving" is the mix generator's template.
+#: The workload shapes: parallel X on 8 and 50 qubits, parallel CNOT on 50
+#: (random and near-solution controls), GHZ on 30 (Sec. III-IV), an echo on 14
+#: qubits whose bonds reach the cap, and the parallel-CNOT gate (operator form).
 WORKLOADS = {
     "x8": Workload("x8", N=8, chi=16, K=20, dt=0.05, C=2, M=16, P=4,
                    noise_dist=0, noise_scale=0.05, seed_u=1, seed_J=2, seed_in=3,
@@ -368,6 +396,16 @@ WORKLOADS = {
     "ghz30": Workload("ghz30", N=30, chi=64, K=200, dt=0.05, C=3, M=512, P=1,
                       noise_dist=0, noise_scale=0.1, seed_u=31, seed_J=32, seed_in=33,
                       target="ghz", g_bonds="all"),
+    # the benchmark shape with near-solution controls: the pi pulse plus N(0, 0.05^2)
+    "cnot50near": Workload("cnot50near", N=50, chi=64, K=100, dt=0.05, C=3, M=256, P=8,
+                           noise_dist=1, noise_scale=0.05, seed_u=21, seed_J=22, seed_in=23,
+                           target="cnot", g_bonds="pairs", u_mode="near"),
+    # bonds at the cap: a 14-qubit echo (random controls, then their time
+    # reverse negated) entangles the middle bonds past chi = 64 (theta up to
+    # 128 x 128), so the cap decides the cut, and returns towards the input
+    "echo14": Workload("echo14", N=14, chi=64, K=16, dt=0.5, C=3, M=304, P=1,
+                       noise_dist=0, noise_scale=0.1, seed_u=51, seed_J=52, seed_in=53,
+                       target="input", g_bonds="all", u_sigma=1.5, u_mode="echo"),
     # the gate objective of Eq. gateinfid with the MPO of Sec. II (D_max = 20)
     "cnotgate50": Workload("cnotgate50", N=50, chi=20, K=100, dt=0.05, C=3, M=256, P=1,
                            noise_dist=1, noise_scale=0.05, seed_u=41, seed_J=42, seed_in=43,

@@ -40,8 +40,9 @@ def test_library_exports_every_declared_symbol(L):
 
 
 def test_status_strings(L):
-    for s in (0, -1, -2, -3, -4, -5, -6):
+    for s in (0, -1, -2, -3, -4, -5, -6, -7):
         assert L.tnrc_status_string(s)
+        assert b"unknown" not in L.tnrc_status_string(s)
     assert b"unknown" in L.tnrc_status_string(42)
 
 

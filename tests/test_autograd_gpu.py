@@ -42,8 +42,9 @@ def test_autograd_matches_oracle_gradient():
 
 
 def test_autograd_central_differences_at_cnot50_scale():
-    """N=50, chi=64, K=100, 3 controls per site, sqrt(K) checkpointing; a
-    2x2 ensemble keeps the 40 extra evaluations short."""
+    """N=50, chi=64, K=100, 3 controls per site (the costate sweep reads the
+    packed forward history; the sqrt-sized checkpoint path is its fallback);
+    a 2x2 ensemble keeps the 40 extra evaluations short."""
     import torch
     from paper_2603_03639_gb300.autograd import fidelity
     w = synth.WORKLOADS["cnot50"].replace(M=2, P=2)
