@@ -364,6 +364,8 @@ def gpu_arm(args, w):
                            "cap_truncations_per_step": capcuts / args.steps, "min_trunc_gap": mingap,
                            "tie_at_cut": bool(mingap is not None and mingap < 1e-10)},
     }
+    if rank == 0 and world == 1 and not args.no_serving:
+        line["serving"] = serving_block(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
@@ -377,26 +379,27 @@ def gpu_arm(args, w):
 # serving leg
 # --------------------------------------------------------------------------
 
-def serving_problems(seed=41):
+def serving_problems(mix="bench", seed=41):
     """Eight resident problems ("optimisers") drawn like the mixed serving
-    workload -- N in {8, 20, 30, 50}, chi in {16, 32, 64}, K, M log-uniform --
-    scaled (K in [20, 50], M in [4, 32]) so that a rate sweep ends in minutes.
-    N=8: parallel X (P=4); N=20: Heisenberg ground state from |0..0> with chi 16
-    (the paper truncates that target at D = 20; at chi 64 its costate grows to
-    64-wide bonds and one request takes minutes); N=30: GHZ; N=50: parallel X
-    or CNOT by the problem's parity."""
+    workload: N in {8, 20, 30, 50} (two of each), chi in {16, 32, 64}, K and M
+    log-uniform.  N=8: parallel X (P=4); N=20: the Heisenberg ground state
+    from |0..0> at the paper's D_max = 20 (chi 20); N=30: GHZ; N=50: parallel
+    X or CNOT by the problem's parity (P=2).
+      mix "bench":   K in [20, 50], M in [4, 32] (a sweep ends in seconds);
+      mix "config5": K in [20, 200], M in [16, 512] (the full ranges)."""
+    lo_k, hi_k, lo_m, hi_m = (20, 50, 4, 32) if mix == "bench" else (20, 200, 16, 512)
     rng = np.random.default_rng(seed)
     probs = []
     heis = {}
     for j in range(8):
         N = [8, 20, 30, 50][j % 4]
         chi = int(rng.choice([16, 32, 64]))
-        K = int(round(np.exp(rng.uniform(np.log(20), np.log(50)))))
-        M = int(round(np.exp(rng.uniform(np.log(4), np.log(32)))))
+        K = int(round(np.exp(rng.uniform(np.log(lo_k), np.log(hi_k)))))
+        M = int(round(np.exp(rng.uniform(np.log(lo_m), np.log(hi_m)))))
         if N == 8:
             w = synth.WORKLOADS["x8"].replace(chi=min(chi, 16), K=K, M=M)
         elif N == 20:
-            w = synth.Workload("heis20", N=20, chi=16, K=K, dt=0.05, C=3, M=M, P=1, noise_dist=0,
+            w = synth.Workload("heis20", N=20, chi=20, K=K, dt=0.05, C=3, M=M, P=1, noise_dist=0,
                                noise_scale=0.05, seed_u=100 + j, seed_J=200 + j, seed_in=300 + j,
                                target="heisenberg", g_bonds="all")
         elif N == 30:
@@ -414,25 +417,48 @@ def serving_problems(seed=41):
     return probs
 
 
-def serving_run(probs, rate, n_req, max_inflight, seed):
-    from paper_2603_03639_gb300.serving import Request, Server, latency_stats
+def serving_requests(probs, rate, n_req, seed):
+    """A Poisson request stream over the resident problems: (arrival times,
+    requests), controls N(0, 0.5^2), own noise seed, half with gradient."""
+    from paper_2603_03639_gb300.serving import Request
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
     reqs = []
-    for i in range(n_req):
+    for _ in range(n_req):
         key, w, ins, tgs = probs[int(rng.integers(len(probs)))]
         reqs.append(Request(key=key, N=w.N, K=w.K, dt=w.dt, chi=w.chi, M=w.M, C=w.C, inputs=ins, targets=tgs,
                             controls=rng.normal(0, 0.5, size=(w.K, w.C, w.N)),
                             noise_seed=int(rng.integers(1 << 40)), noise_dist=w.noise_dist,
                             noise_scale=w.noise_scale, want_grad=bool(rng.integers(2)), mask=w.mask()))
+    return arrivals, reqs
+
+
+def _summary(reqs, rate, extra=None):
+    from paper_2603_03639_gb300.serving import latency_stats
+    st = latency_stats(reqs)
+    st["offered_rps"] = rate
+    # per size class (chain length): p50/p99 latency of that class's requests
+    st["by_N"] = {}
+    for n in sorted({r.N for r in reqs}):
+        sub = latency_stats([r for r in reqs if r.N == n])
+        st["by_N"][str(n)] = {k: sub[k] for k in ("n", "p50_s", "p99_s") if k in sub}
+    if extra:
+        st.update(extra)
+    return st
+
+
+def served_run(probs, arrivals, reqs, max_inflight=8):
+    """The continuous-batching server (pooled launches, priority streams)."""
+    from paper_2603_03639_gb300.serving import Request, Server
     srv = Server(max_inflight=max_inflight)
-    # make every problem resident first (context creation is not request latency)
+    # make every problem resident first (context creation is not request
+    # latency); two warm requests each, so the server knows their sizes
     for key, w, ins, tgs in probs:
-        warm = Request(key=key, N=w.N, K=w.K, dt=w.dt, chi=w.chi, M=w.M, C=w.C, inputs=ins, targets=tgs,
-                       controls=np.zeros((w.K, w.C, w.N)), noise_seed=1, noise_dist=w.noise_dist,
-                       noise_scale=w.noise_scale, want_grad=True, mask=w.mask())
-        srv.submit(warm)
-        srv.drain()
+        for _ in range(2):
+            srv.submit(Request(key=key, N=w.N, K=w.K, dt=w.dt, chi=w.chi, M=w.M, C=w.C, inputs=ins, targets=tgs,
+                               controls=np.zeros((w.K, w.C, w.N)), noise_seed=1, noise_dist=w.noise_dist,
+                               noise_scale=w.noise_scale, want_grad=True, mask=w.mask()))
+            srv.drain()
     t0 = time.perf_counter()
     for r, t in zip(reqs, arrivals):
         now = time.perf_counter() - t0
@@ -442,31 +468,87 @@ def serving_run(probs, rate, n_req, max_inflight, seed):
     srv.drain()
     peak = srv.peak_inflight
     srv.close()
-    st = latency_stats(reqs)
-    st["peak_inflight"] = peak
-    st["offered_rps"] = rate
-    # per size class (chain length): p50/p99 latency of that class's requests
-    st["by_N"] = {}
-    for n in sorted({r.N for r in reqs}):
-        sub = latency_stats([r for r in reqs if r.N == n])
-        st["by_N"][str(n)] = {k: sub[k] for k in ("n", "p50_s", "p99_s") if k in sub}
-    return st, reqs
+    return {"peak_inflight": peak, "high_priority": sum(1 for r in reqs if r.priority == "high")}
+
+
+def plain_run(probs, arrivals, reqs):
+    """Plain sequential GPU calls: the same resident contexts (persistent
+    launch, CUDA graph), one request at a time in arrival order."""
+    import torch
+
+    from paper_2603_03639_gb300 import Context
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+    ctxs = {}
+    F = torch.zeros(1, dtype=torch.float64, device=dev)
+    for key, w, ins, tgs in probs:
+        ctx = Context(w.N, w.K, w.dt, w.chi, w.M, w.C, ins, tgs, cutoff=w.sv_cutoff, mask=w.mask(),
+                      stream=stream.cuda_stream, **form_kwargs(w))
+        ctx.set_graphs(True)
+        g = torch.zeros((w.K, w.C, w.N), dtype=torch.float64, device=dev)
+        for grad in (True, False):           # capture both graphs before the clock starts
+            ctx.set_controls(np.zeros((w.K, w.C, w.N)))
+            ctx.sample_noise(1, w.noise_dist, w.noise_scale)
+            ctx.evaluate_dev(F.data_ptr(), g.data_ptr() if grad else 0)
+            ctx.sync()
+        ctxs[key] = (ctx, g)
+    t0 = time.perf_counter()
+    for r, t in zip(reqs, arrivals):
+        now = time.perf_counter() - t0
+        if t > now:
+            time.sleep(t - now)
+        r.arrival = t0 + t
+        ctx, g = ctxs[r.key]
+        r.start = time.perf_counter()
+        ctx.set_controls(r.controls)
+        ctx.sample_noise(r.noise_seed, r.noise_dist, r.noise_scale)
+        ctx.evaluate_dev(F.data_ptr(), g.data_ptr() if r.want_grad else 0)
+        ctx.sync()
+        r.F = float(F.item())
+        r.grad = g.cpu().numpy().copy() if r.want_grad else None
+        r.finish = time.perf_counter()
+    for ctx, _ in ctxs.values():
+        ctx.close()
+    return {}
+
+
+def serving_compare(probs, rate, n_req, seed):
+    """Served vs plain on one request stream; every result must agree bitwise."""
+    import copy
+    arrivals, reqs = serving_requests(probs, rate, n_req, seed)
+    reqs_p = [copy.copy(r) for r in reqs]
+    ex = served_run(probs, arrivals, reqs)
+    served = _summary(reqs, rate, ex)
+    plain = _summary(reqs_p, rate, plain_run(probs, arrivals, reqs_p))
+    same = all(a.error is None and b.error is None and a.F == b.F
+               and (a.grad is None or np.array_equal(a.grad, b.grad)) for a, b in zip(reqs, reqs_p))
+    return {"offered_rps": rate, "requests": n_req, "served": served, "plain": plain, "results_identical": same}
+
+
+def serving_block(args):
+    """The served half of the metric on the bench mix, for the headline line."""
+    probs = serving_problems("bench")
+    row = serving_compare(probs, args.serve_rate, args.serve_requests, 4242)
+    row["mix"] = [{"key": k, "N": w.N, "chi": w.chi, "K": w.K, "M": w.M, "P": w.P, "target": w.target}
+                  for k, w, _, _ in probs]
+    row["what"] = ("Poisson requests over 8 resident problems (bench mix: N in {8,20,30,50}, K in [20,50], "
+                   "M in [4,32]); served = continuous batching (pooled launches, priority streams); plain = the "
+                   "same requests as sequential GPU calls in arrival order")
+    return row
 
 
 def serving_arm(args):
-    probs = serving_problems()
+    probs = serving_problems(args.mix)
     rates = [float(x) for x in args.rates.split(",")]
     rows = []
     for rate in rates:
-        served, rs = serving_run(probs, rate, args.requests, 8, 1000 + int(rate * 10))
-        print("served at %g req/s: %s" % (rate, served), file=sys.stderr, flush=True)
-        plain, rp = serving_run(probs, rate, args.requests, 1, 1000 + int(rate * 10))
-        print("plain at %g req/s: %s" % (rate, plain), file=sys.stderr, flush=True)
-        same = all(a.F == b.F and (a.grad is None or np.array_equal(a.grad, b.grad)) for a, b in zip(rs, rp))
-        rows.append({"offered_rps": rate, "served": served, "plain": plain, "results_identical": same})
+        row = serving_compare(probs, rate, args.requests, 1000 + int(rate * 10))
+        print("at %g req/s: %s" % (rate, json.dumps(row)), file=sys.stderr, flush=True)
+        rows.append(row)
     line = {"metric": "served p50/p99 latency and throughput vs plain sequential GPU calls",
-            "unit": "s, req/s", "mix": [{"key": k, "N": w.N, "chi": w.chi, "K": w.K, "M": w.M, "P": w.P,
-                                         "target": w.target} for k, w, _, _ in probs],
+            "unit": "s, req/s", "mix_name": args.mix,
+            "mix": [{"key": k, "N": w.N, "chi": w.chi, "K": w.K, "M": w.M, "P": w.P,
+                     "target": w.target} for k, w, _, _ in probs],
             "requests_per_rate": args.requests, "max_inflight": 8, "sweep": rows, "data": "synthetic"}
     print(json.dumps(line), flush=True)
 
@@ -520,8 +602,12 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true", help="serving rate sweep (separate JSON line)")
-    ap.add_argument("--rates", default="1,2,4")
-    ap.add_argument("--requests", type=int, default=16)
+    ap.add_argument("--mix", default="bench", choices=["bench", "config5"], help="serving problem mix")
+    ap.add_argument("--rates", default="8,32")
+    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--no-serving", action="store_true", help="leave the serving block out of the bench line")
+    ap.add_argument("--serve-rate", type=float, default=32.0)
+    ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--plain", action="store_true",
                     help="plain (one CTA) vs batched launch on a sample of the workload (separate JSON line)")
     ap.add_argument("--plain-samples", type=int, default=2)

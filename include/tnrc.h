@@ -66,7 +66,7 @@ typedef int32_t tnrc_status;
 #define TNRC_E_NOMEM (-2)     /* device memory for the context could not be reserved    */
 #define TNRC_E_CUDA (-3)      /* a CUDA call failed; the context is unusable             */
 #define TNRC_E_STATE (-4)     /* controls or noise not set yet                           */
-#define TNRC_E_TIMEOUT (-5)   /* reserved: no entry point waits on the device unbounded  */
+#define TNRC_E_TIMEOUT (-5)   /* a bounded device wait gave up (pooled launch)           */
 #define TNRC_E_NUMERIC (-6)   /* Jacobi SVD did not converge, or a NaN/Inf appeared      */
 #define TNRC_E_TOO_LARGE (-7) /* problem exceeds the fixed scratch of tnrc_fidelity_static */
 
@@ -133,10 +133,11 @@ typedef struct {
   int64_t restarts;              /* trajectories of the last evaluation whose forward history
                                     did not fit their CTA's region packed and that were redone
                                     with checkpoints (results are identical either way)     */
-  int64_t phase_cycles[8];       /* SM cycles summed over warps per phase of the trajectory
-                                    kernel (contraction, Jacobi, rank/truncate, split,
+  int64_t phase_cycles[9];       /* SM cycles summed over warps per phase of the trajectory
+                                    kernel (contraction, pivoted QR, rank/truncate, split,
                                     environments, gradients, history copies, layer
-                                    barriers); zero unless built with TNRC_PHASE_TIMERS   */
+                                    barriers, Jacobi sweeps); zero unless built with
+                                    TNRC_PHASE_TIMERS                                       */
   int64_t cap_truncations;       /* truncations of the last evaluation (forward and costate
                                     updates) whose cut the cap decided: more singular values
                                     exceeded the cutoff than chi_max keeps (Sec. II, D_max)  */
@@ -208,6 +209,26 @@ tnrc_status tnrc_evaluate_dev(tnrc_ctx* ctx, double* d_F, double* d_grad, double
  * an application's own stream capture.  Errors: TNRC_E_INVALID when enabling
  * on a context created on the legacy default stream (it cannot be captured). */
 tnrc_status tnrc_set_graphs(tnrc_ctx* ctx, int32_t enable);
+
+/* Order the context's later work on another stream (a cudaStream_t; NULL =
+ * the legacy default stream, refused while graphs are on).  Waits for the
+ * work already queued on the current stream first.  A serving loop uses it
+ * to run one problem's requests at the priority each request deserves. */
+tnrc_status tnrc_set_stream(tnrc_ctx* ctx, void* cuda_stream);
+
+/* Launch the trajectory kernel pooled (enable = 1) or persistent (0, the
+ * default).  Persistent: one CTA per resident slot, each taking trajectories
+ * from a device counter until none are left -- the fastest form for one
+ * evaluation alone, but its CTAs hold their SMs until the evaluation ends.
+ * Pooled: one CTA per trajectory; a CTA takes one of the context's work
+ * regions from a device pool while it runs (a bounded wait; TNRC_E_TIMEOUT if
+ * it ever gave up) and hands it back when its trajectory is done, so the
+ * block scheduler can start CTAs of other launches -- another context's
+ * request on a higher-priority stream -- between trajectories.  Results are
+ * bitwise the same in both forms.  Captured graphs are dropped when the form
+ * changes.  Errors: TNRC_E_INVALID when the context's work regions cannot
+ * cover the CTAs that could be resident at once (a memory-limited context). */
+tnrc_status tnrc_set_pooled(tnrc_ctx* ctx, int32_t enable);
 
 /* Synchronise the context's stream and report any device-side error flag. */
 tnrc_status tnrc_sync(tnrc_ctx* ctx);

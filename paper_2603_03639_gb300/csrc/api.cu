@@ -16,6 +16,7 @@
 
 extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, size_t smem, cudaStream_t st);
 extern "C" cudaError_t tnrc_traj_prepare();
+extern "C" cudaError_t tnrc_traj_occupancy(int phys_dim, int min_blocks, int warps, size_t smem, int* per_sm);
 extern "C" cudaError_t tnrc_launch_layer_gates(int N, int K, int C, int M, int terms, int order, int nsub,
                                                int L, int R, int first_parity, double dt, const double* u,
                                                const unsigned char* mask, const double* gfix, const double* J,
@@ -50,6 +51,10 @@ struct tnrc_ctx {
     cudaGraphExec_t exec;
   };
   bool use_graphs = false;
+  // pooled launch (one CTA per trajectory, work regions from a pool), with
+  // the dynamic shared memory that keeps the resident CTAs within the pool
+  bool pooled = false;
+  size_t pooled_smem = 0;
   bool timed_last = false;        // ev0/ev1 bracket the last evaluation (not a graph replay)
   std::vector<GraphEntry> graphs;
   char err[256] = {0};            // the CUDA failure that made the context unusable
@@ -133,10 +138,19 @@ tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, dou
   tp.counters = ctx->at<unsigned long long>(P.off_counters);
   tp.status = ctx->at<int>(P.off_status);
   tp.work_counter = ctx->at<int>(P.off_wc);
-  const size_t smem = tnrc_traj_smem(P.warps, P.slab_elems);
+  size_t smem = tnrc_traj_smem(P.warps, P.slab_elems);
+  int grid = P.grid;
+  if (ctx->pooled) {
+    tp.pooled = 1;
+    tp.n_regions = P.grid;
+    tp.region_owner = ctx->at<int>(P.off_owner);
+    CK(cudaMemsetAsync(tp.region_owner, 0, (size_t)P.grid * 4, st));
+    smem = ctx->pooled_smem;
+    grid = P.T;
+  }
   const bool timed = !capturing && ctx->tev_used + 2 <= ctx->tev.size();
   if (timed) CK(cudaEventRecord(ctx->tev[ctx->tev_used], st));
-  CK(tnrc_launch_traj(&tp, P.grid, smem, st));
+  CK(tnrc_launch_traj(&tp, grid, smem, st));
   if (timed) {
     CK(cudaEventRecord(ctx->tev[ctx->tev_used + 1], st));
     ctx->tev_used += 2;
@@ -185,7 +199,7 @@ tnrc_status finish(tnrc_ctx* ctx) {
   if (status) {
     CK(cudaMemset(ctx->at<int>(ctx->plan.off_status), 0, sizeof(int)));
     ctx->last_status = status;
-    return TNRC_E_NUMERIC;
+    return (status & tnrc::kStatusTimeout) ? TNRC_E_TIMEOUT : TNRC_E_NUMERIC;
   }
   float ms = 0.f;
   if (ctx->timed_last) CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
@@ -437,6 +451,46 @@ tnrc_status tnrc_set_graphs(tnrc_ctx* ctx, int32_t enable) {
   if (ctx->broken) return TNRC_E_CUDA;
   if (enable && ctx->stream == nullptr) return TNRC_E_INVALID;  // the legacy stream cannot be captured
   ctx->use_graphs = enable != 0;
+  return TNRC_OK;
+}
+
+tnrc_status tnrc_set_stream(tnrc_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return TNRC_E_INVALID;
+  if (ctx->broken) return TNRC_E_CUDA;
+  if (ctx->use_graphs && cuda_stream == nullptr) return TNRC_E_INVALID;   // the legacy stream cannot be captured
+  CK(cudaStreamSynchronize(ctx->stream));   // work already queued stays ordered before the switch
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return TNRC_OK;
+}
+
+tnrc_status tnrc_set_pooled(tnrc_ctx* ctx, int32_t enable) {
+  if (!ctx || (enable != 0 && enable != 1)) return TNRC_E_INVALID;
+  if (ctx->broken) return TNRC_E_CUDA;
+  const Plan& P = ctx->plan;
+  if (enable && !ctx->pooled) {
+    // the pool holds P.grid regions: no more CTAs than that may be resident,
+    // so ask for enough dynamic shared memory to keep the occupancy there
+    int dev = 0, smem_sm = 0, occ = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    const int tp_min_blocks = P.d == 4 ? 1 : P.min_blocks;
+    const size_t base = tnrc_traj_smem(P.warps, P.slab_elems);
+    const int per_sm_max = std::max(1, P.grid / std::max(1, ctx->n_sm));
+    size_t smem = base;
+    CK(tnrc_traj_occupancy(P.d, tp_min_blocks, P.warps, smem, &occ));
+    if ((long long)occ * ctx->n_sm > P.grid && P.T > P.grid) {
+      smem = std::max(base, (size_t)(smem_sm / per_sm_max) - 4096);
+      smem = std::min<size_t>(smem, 226 * 1024);
+      CK(tnrc_traj_occupancy(P.d, tp_min_blocks, P.warps, smem, &occ));
+      if ((long long)occ * ctx->n_sm > P.grid) return TNRC_E_INVALID;
+    }
+    ctx->pooled_smem = smem;
+  }
+  if (ctx->pooled != (enable != 0)) {
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);   // captured with the other launch
+    ctx->graphs.clear();
+  }
+  ctx->pooled = enable != 0;
   return TNRC_OK;
 }
 

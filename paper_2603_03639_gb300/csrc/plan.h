@@ -74,7 +74,8 @@ struct Plan {
   // arena offsets (bytes)
   int64_t off_loff;
   int64_t off_u, off_mask, off_gfix, off_J, off_gates, off_in, off_tg, off_work, off_scratch, off_env, off_O,
-      off_gsp, off_disc, off_counters, off_status, off_wc, off_F, off_grad, off_per, off_siteoff, off_dcap, total;
+      off_gsp, off_disc, off_counters, off_status, off_wc, off_F, off_grad, off_per, off_siteoff, off_dcap,
+      off_owner, total;
 };
 
 inline bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan& P, bool limit_by_memory) {
@@ -196,6 +197,7 @@ inline bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan&
   P.off_work = take((int64_t)P.grid * P.work_stride);
   P.off_scratch = take((int64_t)P.grid * P.warps * P.scratch_elems * 16);
   P.off_env = take((int64_t)P.grid * P.env_elems * 16);
+  P.off_owner = take((int64_t)P.grid * 4);   // region pool of the pooled launch
   P.total = off;
   return true;
 }

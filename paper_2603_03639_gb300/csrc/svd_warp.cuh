@@ -5,10 +5,10 @@
 // The matrix is held column-major (column j at T + j*n, n rows).  Its m
 // columns are orthogonalised by plane rotations in the round-robin (circle)
 // ordering, m/2 disjoint pairs per round, so that a whole round runs in
-// parallel: each pair gets g lanes (g a power of two, g * pairs <= 32), each
-// lane owns rows lig, lig+g, ...; the three inner products of a pair are
-// reduced over its g lanes with xor shuffles (bitwise identical in every lane,
-// so every lane takes the same decision).  After convergence column j equals
+// parallel: each pair gets g lanes (g * pairs <= 32), each lane owns rows
+// lig, lig+g, ...; the three inner products of a pair are reduced over its g
+// lanes by shuffles (bitwise identical in every lane, so every lane takes the
+// same decision).  After convergence column j equals
 // sigma_j y_j with y_j orthonormal: for T = M^dagger, y_j are the right
 // singular vectors of M and sigma_j its singular values.
 #pragma once
@@ -27,9 +27,57 @@ __device__ __forceinline__ void rr_pair(int mp, int r, int q, int& i, int& j) {
   }
 }
 
-// Returns the number of sweeps (the last one made no rotation), or -kMaxSweeps
+// Sum of v over the g lanes gb .. gb+g-1 of this lane's group (lig = lane -
+// gb, gmask = those lanes); every lane of the group receives the same value.
+// A power-of-two g uses an xor butterfly; any other g a shift-down tree into
+// lane gb and a broadcast from it (a source lane outside the group is never
+// added).
+__device__ __forceinline__ double group_sum(double v, int g, int lig, int gb, unsigned gmask) {
+  if ((g & (g - 1)) == 0) {
+    for (int o = g >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o);
+    return v;
+  }
+  int o = 1;
+  while (2 * o < g) o <<= 1;
+  for (; o > 0; o >>= 1) {
+    const double x = __shfl_down_sync(gmask, v, o);
+    if (lig + o < g) v += x;
+  }
+  return __shfl_sync(gmask, v, gb);
+}
+
+__device__ __forceinline__ unsigned group_mask(int g, int gb) {
+  return (g >= 32) ? 0xffffffffu : (((1u << g) - 1u) << gb);
+}
+
+// out[c] = |column c|^2 for the m columns of length n of T (column-major),
+// with g = 32 / m lanes per column (any g), so that short columns keep most
+// lanes busy.
+__device__ inline void warp_col_norms(const double2* T, int n, int m, double* out, int lane) {
+  const int g = (m >= 32 || m < 1) ? 1 : 32 / m;
+  const int gi = lane / g, lig = lane - gi * g, gb = gi * g;
+  const int groups = 32 / g;
+  const unsigned gmask = group_mask(g, gb);
+  for (int c = gi; c < m && gi < groups; c += groups) {
+    const double2* col = T + (size_t)c * n;
+    double s = 0.0;
+    for (int row = lig; row < n; row += g) s = fma(col[row].x, col[row].x, fma(col[row].y, col[row].y, s));
+    if (g > 1) s = group_sum(s, g, lig, gb, gmask);
+    if (lig == 0) out[c] = s;
+  }
+  __syncwarp();
+}
+
+// Returns the number of sweeps (the last one made no rotation, or only
+// rotations with |cos| <= 1e-10 between the pair's columns), or -kMaxSweeps
 // when the sweep limit was reached.  fro2 = squared Frobenius norm of T;
 // cn: shared scratch of m doubles holding the column norms squared.
+//
+// Lanes per pair: an odd m is padded with a zero column, which the circle
+// ordering pairs with a different real column in every round (pair q = 0);
+// that pair needs no work, so the Pe = floor(m / 2) real pairs of a round
+// share the 32 lanes, g = floor(32 / Pe) each (not necessarily a power of
+// two).  Each lane then owns ceil(n / g) rows of its pair.
 //
 // The norms are computed exactly before the first sweep and in the first
 // round of every sweep (where the pair's lanes form all three inner
@@ -41,28 +89,23 @@ __device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, double*
   const int mp = m + (m & 1);
   if (mp < 2 || n < 1) return 0;
   const int P = mp >> 1;
-  int g = 1;
-  while (g < 32 && g * 2 * P <= 32) g <<= 1;
+  const int q0 = m & 1;          // pair 0 holds the padding column of an odd m
+  const int Pe = P - q0;         // real pairs per round
+  if (Pe < 1) return 1;          // a single column is already orthogonal
+  const int g = Pe >= 32 ? 1 : 32 / Pe;
   const int groups = 32 / g;
-  const int lig = lane & (g - 1);
-  const unsigned gmask = (g == 32) ? 0xffffffffu : (((1u << g) - 1u) << (lane & ~(g - 1)));
+  const int gi = lane / g, lig = lane - gi * g, gb = gi * g;
+  const unsigned gmask = group_mask(g, gb);
   const double thr = kJacobiZero * kJacobiZero * fro2;
   const double tol = 2.0 * (double)(m > n ? m : n) * 2.220446049250313e-16;
   const double tol2 = tol * tol;
-  for (int c = lane; c < m; c += 32) {
-    const double2* col = T + (size_t)c * n;
-    double s = 0.0;
-    for (int row = 0; row < n; ++row) s = fma(col[row].x, col[row].x, fma(col[row].y, col[row].y, s));
-    cn[c] = s;
-  }
-  __syncwarp();
+  warp_col_norms(T, n, m, cn, lane);
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-    int rotated = 0;
+    int rotated = 0, large = 0;
     for (int r = 0; r < mp - 1; ++r) {
-      for (int q = lane / g; q < P; q += groups) {
+      for (int q = q0 + gi; q < P && gi < groups; q += groups) {
         int i, j;
         rr_pair(mp, r, q, i, j);
-        if (i >= m || j >= m) continue;  // the padding column of an odd m is zero
         double2* a = T + (size_t)i * n;
         double2* b = T + (size_t)j * n;
         double aa, bb;
@@ -76,25 +119,27 @@ __device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, double*
             bb = fma(y.x, y.x, fma(y.y, y.y, bb));
             cfmac(ab, x, y);
           }
-          for (int o = g >> 1; o > 0; o >>= 1) {
-            aa += __shfl_xor_sync(gmask, aa, o);
-            bb += __shfl_xor_sync(gmask, bb, o);
-            ab.x += __shfl_xor_sync(gmask, ab.x, o);
-            ab.y += __shfl_xor_sync(gmask, ab.y, o);
+          if (g > 1) {
+            aa = group_sum(aa, g, lig, gb, gmask);
+            bb = group_sum(bb, g, lig, gb, gmask);
+            ab.x = group_sum(ab.x, g, lig, gb, gmask);
+            ab.y = group_sum(ab.y, g, lig, gb, gmask);
           }
         } else {
           aa = cn[i];
           bb = cn[j];
           for (int row = lig; row < n; row += g) cfmac(ab, a[row], b[row]);
-          for (int o = g >> 1; o > 0; o >>= 1) {
-            ab.x += __shfl_xor_sync(gmask, ab.x, o);
-            ab.y += __shfl_xor_sync(gmask, ab.y, o);
+          if (g > 1) {
+            ab.x = group_sum(ab.x, g, lig, gb, gmask);
+            ab.y = group_sum(ab.y, g, lig, gb, gmask);
           }
         }
         double na = aa, nb = bb;
         const double ab2 = cabs2(ab);
-        if (aa > thr && bb > thr && ab2 > tol2 * aa * bb) {
+        const double pab = aa * bb;
+        if (aa > thr && bb > thr && ab2 > tol2 * pab) {
           rotated = 1;
+          large |= (ab2 > kJacobiQuad * pab) ? 1 : 0;
           // Real rotation of the pair after the phase of <a,b> is divided out,
           // cot(2 theta) = (|b|^2 - |a|^2) / (2 |<a,b>|).  With d = |b|^2 - |a|^2
           // and w = 1 / sqrt(d^2 + 4 |<a,b>|^2): cos 2theta = |d| w,
@@ -128,12 +173,12 @@ __device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, double*
           if (na < 0.0625 * aa) {
             na = 0.0;
             for (int row = lig; row < n; row += g) na = fma(a[row].x, a[row].x, fma(a[row].y, a[row].y, na));
-            for (int o = g >> 1; o > 0; o >>= 1) na += __shfl_xor_sync(gmask, na, o);
+            if (g > 1) na = group_sum(na, g, lig, gb, gmask);
           }
           if (nb < 0.0625 * bb) {
             nb = 0.0;
             for (int row = lig; row < n; row += g) nb = fma(b[row].x, b[row].x, fma(b[row].y, b[row].y, nb));
-            for (int o = g >> 1; o > 0; o >>= 1) nb += __shfl_xor_sync(gmask, nb, o);
+            if (g > 1) nb = group_sum(nb, g, lig, gb, gmask);
           }
         }
         if (lig == 0) {
@@ -143,7 +188,11 @@ __device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, double*
       }
       __syncwarp();
     }
-    if (!__any_sync(0xffffffffu, rotated)) return sweep + 1;
+    // converged: a sweep without rotations -- or one whose rotations all had
+    // |cos| <= 1e-10 between the pair's columns, after which (the cyclic
+    // method converging quadratically) the next sweep would find every
+    // |cos| near 1e-20, far below tol, and rotate nothing
+    if (!__any_sync(0xffffffffu, rotated) || !__any_sync(0xffffffffu, large)) return sweep + 1;
   }
   return -kMaxSweeps;
 }
@@ -157,11 +206,12 @@ __device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, double*
 //
 // Step j takes the remaining column of largest norm as pivot; when that norm
 // squared is <= thr, every remaining column is below it and the
-// factorisation stops with r = j.  Columns are shared out to groups of G lanes
-// (G * n <= 32 when n <= 32), each group's lanes splitting the rows; the
-// trailing column norms are recomputed exactly while the reflector is applied,
-// so the pivot choice needs no norm downdating.  Reductions within a group use
-// xor shuffles, so every lane of a group holds the same sums, and the pivot
+// factorisation stops with r = j.  The trailing columns of a step are shared
+// out to groups of G = floor(32 / columns) lanes, each group's lanes
+// splitting the rows; the trailing column norms are recomputed exactly while
+// the reflector is applied,
+// so the pivot choice needs no norm downdating.  Reductions within a group
+// leave the same sums in every lane of the group, and the pivot
 // reduction (integer comparisons of the non-negative norms' bit patterns, ties
 // to the smaller index) gives every lane the same pivot.
 //
@@ -169,18 +219,19 @@ __device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, double*
 // j-th row of R in the pivoted column order), piv[c] is the original index of
 // pivoted column c (c < n), and qn (n doubles) has been used as scratch.
 __device__ inline int warp_qrcp(double2* W, int m, int n, double thr, int* piv, double* qn, int lane) {
-  int G = 1;
-  while (G < 32 && G * 2 * n <= 32) G <<= 1;
-  const int groups = 32 / G;
-  const int gi = lane / G, lig = lane & (G - 1);
-  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-  for (int c = gi; c < n; c += groups) {
-    double q = 0.0;
-    for (int i = lig; i < m; i += G) q += cabs2(W[(size_t)i * n + c]);
-    for (int o = G >> 1; o > 0; o >>= 1) q += __shfl_xor_sync(gmask, q, o);
-    if (lig == 0) {
-      qn[c] = q;
-      piv[c] = c;
+  {
+    const int G = n >= 32 ? 1 : 32 / n;
+    const int groups = 32 / G;
+    const int gi = lane / G, lig = lane - gi * G, gb = gi * G;
+    const unsigned gmask = group_mask(G, gb);
+    for (int c = gi; c < n && gi < groups; c += groups) {
+      double q = 0.0;
+      for (int i = lig; i < m; i += G) q += cabs2(W[(size_t)i * n + c]);
+      if (G > 1) q = group_sum(q, G, lig, gb, gmask);
+      if (lig == 0) {
+        qn[c] = q;
+        piv[c] = c;
+      }
     }
   }
   __syncwarp();
@@ -229,31 +280,39 @@ __device__ inline int warp_qrcp(double2* W, int m, int n, double thr, int* piv, 
     const double2 ph = (ax0 > 0.0) ? cscale(x0, 1.0 / ax0) : make_double2(1.0, 0.0);
     const double2 v0 = cscale(ph, ax0 + xn);
     const double beta = 1.0 / (xn * (xn + ax0));
-    for (int c = gi; c < n; c += groups) {
-      if (c <= j) continue;
-      double2 s = make_double2(0.0, 0.0);
-      for (int i = j + lig; i < m; i += G) {
-        const double2 vi = (i == j) ? v0 : W[(size_t)i * n + j];
-        cfmac(s, vi, W[(size_t)i * n + c]);
+    // the na = n - j - 1 trailing columns share the 32 lanes, G = 32 / na
+    // lanes each (any G), so that the lanes stay busy as the columns run out
+    const int na = n - j - 1;
+    if (na > 0) {
+      const int G = na >= 32 ? 1 : 32 / na;
+      const int groups = 32 / G;
+      const int gi = lane / G, lig = lane - gi * G, gb = gi * G;
+      const unsigned gmask = group_mask(G, gb);
+      for (int c = j + 1 + gi; c < n && gi < groups; c += groups) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int i = j + lig; i < m; i += G) {
+          const double2 vi = (i == j) ? v0 : W[(size_t)i * n + j];
+          cfmac(s, vi, W[(size_t)i * n + c]);
+        }
+        if (G > 1) {
+          s.x = group_sum(s.x, G, lig, gb, gmask);
+          s.y = group_sum(s.y, G, lig, gb, gmask);
+        }
+        s = cscale(s, beta);
+        double q = 0.0;
+        for (int i = j + lig; i < m; i += G) {
+          const double2 vi = (i == j) ? v0 : W[(size_t)i * n + j];
+          double2 x = W[(size_t)i * n + c];
+          x.x = fma(-vi.x, s.x, x.x);
+          x.x = fma(vi.y, s.y, x.x);
+          x.y = fma(-vi.x, s.y, x.y);
+          x.y = fma(-vi.y, s.x, x.y);
+          W[(size_t)i * n + c] = x;
+          if (i > j) q += cabs2(x);
+        }
+        if (G > 1) q = group_sum(q, G, lig, gb, gmask);
+        if (lig == 0) qn[c] = q;
       }
-      for (int o = G >> 1; o > 0; o >>= 1) {
-        s.x += __shfl_xor_sync(gmask, s.x, o);
-        s.y += __shfl_xor_sync(gmask, s.y, o);
-      }
-      s = cscale(s, beta);
-      double q = 0.0;
-      for (int i = j + lig; i < m; i += G) {
-        const double2 vi = (i == j) ? v0 : W[(size_t)i * n + j];
-        double2 x = W[(size_t)i * n + c];
-        x.x = fma(-vi.x, s.x, x.x);
-        x.x = fma(vi.y, s.y, x.x);
-        x.y = fma(-vi.x, s.y, x.y);
-        x.y = fma(-vi.y, s.x, x.y);
-        W[(size_t)i * n + c] = x;
-        if (i > j) q += cabs2(x);
-      }
-      for (int o = G >> 1; o > 0; o >>= 1) q += __shfl_xor_sync(gmask, q, o);
-      if (lig == 0) qn[c] = q;
     }
     __syncwarp();
     for (int i = j + lane; i < m; i += 32)
@@ -273,13 +332,7 @@ __device__ inline int warp_qrcp(double2* W, int m, int n, double thr, int* piv, 
 // the first dropped value; otherwise gap = -1.
 __device__ inline int warp_rank_truncate(const double2* T, int n, int m, int kcap, double eps, double* sig2,
                                   int* perm, int lane, double& kept2, double& tot2, double& gap) {
-  for (int j = lane; j < m; j += 32) {
-    const double2* c = T + (size_t)j * n;
-    double s = 0.0;
-    for (int r = 0; r < n; ++r) s = fma(c[r].x, c[r].x, fma(c[r].y, c[r].y, s));
-    sig2[j] = s;
-  }
-  __syncwarp();
+  warp_col_norms(T, n, m, sig2, lane);
   double mx = 0.0, tot = 0.0;
   for (int j = lane; j < m; j += 32) {
     mx = fmax(mx, sig2[j]);

@@ -20,22 +20,27 @@ constexpr int kWarps = 8;                   // warps per trajectory CTA (upper b
 constexpr int kMaxSweeps = 60;              // Jacobi sweep limit
 constexpr double kZeroFloor = 1e-13;        // relative numerical-zero level of singular values
 constexpr double kJacobiZero = 5e-15;       // columns below this x ||theta||_F are left alone
+constexpr double kJacobiQuad = 1e-20;       // |<a,b>|^2 / (|a|^2 |b|^2) of a rotation that counts as
+                                            // large: a sweep with none is the last (quadratic convergence)
 
 // device status bits (OR-ed into *status)
 constexpr int kStatusNoConverge = 1;
 constexpr int kStatusNaN = 2;
 constexpr int kStatusBadDims = 4;
+constexpr int kStatusTimeout = 8;            // a bounded device wait gave up (no free work region)
+constexpr int kRegionTries = 1 << 16;        // region-pool scans before giving up (about a second)
 constexpr int kCtrPhase = 5 + kMaxChi + 1;      // first of kNumPhases cycle counters
-constexpr int kNumPhases = 8;
+constexpr int kNumPhases = 9;
 constexpr int kCtrCapTrunc = kCtrPhase + kNumPhases;  // truncations whose cut the cap chi_max decided
 constexpr int kCtrGap = kCtrCapTrunc + 1;              // smallest relative gap at such a cut (double bits;
                                                        // starts as all ones, lowered by atomicMin)
 constexpr int kNumCounters = kCtrGap + 1;              // device counters of one evaluation
 
 // Per-phase cycle counters (lane 0 of every warp, clock64), compiled in only
-// with -DTNRC_PHASE_TIMERS: 0 contraction, 1 Jacobi sweeps, 2 rank/truncate,
+// with -DTNRC_PHASE_TIMERS: 0 contraction, 1 pivoted QR, 2 rank/truncate,
 // 3 split and write-back, 4 environment sweeps, 5 mixed densities and gate
-// gradients, 6 history and slot copies, 7 waiting at layer barriers.
+// gradients, 6 history and slot copies, 7 waiting at layer barriers,
+// 8 Jacobi sweeps.
 #ifdef TNRC_PHASE_TIMERS
 #define TNRC_TIC(v) const long long v = clock64()
 #define TNRC_TOC(w, idx, v) \
@@ -116,6 +121,14 @@ struct TrajParams {
   unsigned long long* counters;    // see kCtrHist in traj.cu
   int* status;
   int* work_counter;
+  // launch mode: 0 = persistent (grid <= resident CTAs; each CTA takes
+  // trajectories from work_counter and uses the work region of its index);
+  // 1 = pooled (one CTA per trajectory, t = blockIdx.x; the CTA holds one of
+  // n_regions work regions from region_owner while it runs, so the block
+  // scheduler can interleave CTAs of other launches between trajectories)
+  int pooled;
+  int n_regions;
+  int* region_owner;               // [n_regions], 0 = free
 };
 
 struct CanonArgs {

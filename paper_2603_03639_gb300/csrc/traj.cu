@@ -48,6 +48,7 @@ struct WarpCtx {
   long long ph[kNumPhases]; // phase cycles (TNRC_PHASE_TIMERS builds)
   int* order;               // shared, CTA-wide: bonds of the current layer by decreasing cost
   int* next;                // shared, CTA-wide: next entry of `order` to take
+  int region;               // the CTA's work region (scratch, environments, slots)
 };
 
 // Algorithmic flops of one two-site update with theta of m x n (m = 2 Dl,
@@ -156,8 +157,10 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   if (r < 1) r = 1;  // theta == 0 (or not finite): keep one column; the NaN check below reports it
   for (int e = lane; e < r * n; e += 32) T[e] = cconj(T[e]);
   __syncwarp();
-  const int sw = warp_jacobi(T, n, r, fro, w.qn, lane);   // qn is free after the QR
   TNRC_TOC(w, 1, t_j);
+  TNRC_TIC(t_s);
+  const int sw = warp_jacobi(T, n, r, fro, w.qn, lane);   // qn is free after the QR
+  TNRC_TOC(w, 8, t_s);
 
   // Phase 3: rank, truncate.
   TNRC_TIC(t_r);
@@ -189,15 +192,21 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   TNRC_TOC(w, 2, t_r);
 
   // Phase 4: write lam_b, B_{b+1} = Y_k^dag, B_b = Phi Y_k / |S_k|, where
-  // Y[piv[c]][i] = Z[c][i] = T[perm[i] n + c] / sigma_i.
+  // Y[piv[c]][i] = Z[c][i] = T[perm[i] n + c] / sigma_i (1 / sigma_i once per
+  // kept value, in qn, which the Jacobi no longer needs).
   TNRC_TIC(t_w);
   double* lamw = lam + (size_t)b * lstride;
   const int* piv = w.piv;
-  for (int i = lane; i < k; i += 32) lamw[i] = sqrt(w.sig2[w.perm[i]]) * inv_kn;
+  double* isig = w.qn;
+  for (int i = lane; i < k; i += 32) {
+    lamw[i] = sqrt(w.sig2[w.perm[i]]) * inv_kn;
+    isig[i] = rsqrt(w.sig2[w.perm[i]]);
+  }
+  __syncwarp();
   for (int it = lane; it < k * n; it += 32) {
     const int i = it / n, c = it - i * n;
     const int j = w.perm[i];
-    Bt[(size_t)i * n + piv[c]] = cscale(cconj(T[(size_t)j * n + c]), rsqrt(w.sig2[j]));
+    Bt[(size_t)i * n + piv[c]] = cscale(cconj(T[(size_t)j * n + c]), isig[i]);
   }
   for (int it = lane; it < m * k; it += 32) {
     const int row = it / k, i = it - row * k;
@@ -206,7 +215,7 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
     const double2* z = T + (size_t)j * n;
     double2 acc = make_double2(0.0, 0.0);
     for (int c = 0; c < n; ++c) cfma(acc, ph[piv[c]], z[c]);
-    A[it] = cscale(acc, rsqrt(w.sig2[j]) * inv_kn);
+    A[it] = cscale(acc, isig[i] * inv_kn);
   }
   __syncwarp();
   if (lane == 0) D[b + 1] = k;
@@ -365,7 +374,7 @@ __device__ void layer_gradient(const TrajParams& p, const Lay& Y, const unsigned
   const double2* as = av.sites;
   const int* so = Y.site_off;   // costate slot offsets
   const int* ao = av.off;       // forward-state offsets
-  double2* Lbuf = p.env_scratch + (size_t)blockIdx.x * 2 * (N + 1) * cc;
+  double2* Lbuf = p.env_scratch + (size_t)w.region * 2 * (N + 1) * cc;
   double2* Rbuf = Lbuf + (size_t)(N + 1) * cc;
   const int lane = w.lane;
 
@@ -684,6 +693,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) traj_kernel(TrajParam
   __shared__ double2 s_O;
   __shared__ int s_order[128];
   __shared__ int s_next;
+  __shared__ int s_region;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   double2* slabs = reinterpret_cast<double2*>(smem_raw);
@@ -693,9 +703,36 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) traj_kernel(TrajParam
   int* pivs = perms + (size_t)p.warps * kMaxDim;
   double2* smalls = reinterpret_cast<double2*>(pivs + (size_t)p.warps * kMaxDim);
 
+  // pooled launch: take a free work region (bounded scan; a full pool cannot
+  // happen while n_regions covers the CTAs that can be resident at once)
+  int region = blockIdx.x;
+  if (p.pooled) {
+    if (blockIdx.x >= p.T) return;
+    if (threadIdx.x == 0) {
+      int got = -1;
+      for (int attempt = 0; attempt < kRegionTries && got < 0; ++attempt) {
+        for (int i = 0; i < p.n_regions; ++i) {
+          const int r = (int)((blockIdx.x + (unsigned)i) % (unsigned)p.n_regions);
+          if (atomicCAS(&p.region_owner[r], 0, 1) == 0) {
+            got = r;
+            break;
+          }
+        }
+        if (got < 0) __nanosleep(16000);
+      }
+      s_region = got;
+    }
+    __syncthreads();
+    region = s_region;
+    if (region < 0) {
+      if (threadIdx.x == 0) atomicOr(p.status, kStatusTimeout);
+      return;
+    }
+  }
   WarpCtx w;
+  w.region = region;
   w.slab = slabs + (size_t)warp * p.slab_elems;
-  w.scratch = p.warp_scratch + ((size_t)blockIdx.x * p.warps + warp) * p.scratch_elems;
+  w.scratch = p.warp_scratch + ((size_t)region * p.warps + warp) * p.scratch_elems;
   w.sig2 = sig + (size_t)warp * kMaxDim;
   w.perm = perms + (size_t)warp * kMaxDim;
   w.qn = qns + (size_t)warp * kMaxDim;
@@ -709,10 +746,10 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) traj_kernel(TrajParam
   for (int i = 0; i < kNumPhases; ++i) w.ph[i] = 0;
   w.order = s_order;
   w.next = &s_next;
-  unsigned char* base = p.work + (size_t)blockIdx.x * p.work_stride;
+  unsigned char* base = p.work + (size_t)region * p.work_stride;
 
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(p.work_counter, 1);
+  for (int iter = 0;; ++iter) {
+    if (threadIdx.x == 0) s_item = p.pooled ? (iter == 0 ? (int)blockIdx.x : p.T) : atomicAdd(p.work_counter, 1);
     __syncthreads();
     const int t = s_item;
     __syncthreads();
@@ -742,25 +779,36 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) traj_kernel(TrajParam
     for (int i = 0; i < kNumPhases; ++i) atomicAdd(&p.counters[kCtrPhase + i], (unsigned long long)w.ph[i]);
 #endif
   }
+  if (p.pooled) {   // hand the region back once every thread is done with it
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicExch(&p.region_owner[region], 0);
+    }
+  }
 }
 
 }  // namespace tnrc
 
-// host-side launcher; the shared-memory limit is raised once per device and
-// process (tnrc_create calls tnrc_traj_prepare before any launch or capture)
+// host-side launcher; tnrc_create (and the allocation-free entry point) raise
+// the shared-memory limit with tnrc_traj_prepare before any launch or capture
 extern "C" cudaError_t tnrc_traj_prepare() {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  static bool attr_set[64] = {false};
-  if (dev >= 0 && dev < 64 && attr_set[dev]) return cudaSuccess;
-  e = cudaFuncSetAttribute(tnrc::traj_kernel<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(tnrc::traj_kernel<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(tnrc::traj_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(tnrc::traj_kernel<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
-  if (e == cudaSuccess && dev >= 0 && dev < 64) attr_set[dev] = true;
   return e;
+}
+
+// Resident CTAs per SM of the trajectory kernel for this launch shape (the
+// size of a pooled launch's region pool is SMs times this).
+extern "C" cudaError_t tnrc_traj_occupancy(int phys_dim, int min_blocks, int warps, size_t smem, int* per_sm) {
+  if (phys_dim == 4)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, tnrc::traj_kernel<1, 4>, warps * 32, smem);
+  if (min_blocks == 2)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, tnrc::traj_kernel<2, 2>, warps * 32, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, tnrc::traj_kernel<1, 2>, warps * 32, smem);
 }
 
 extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, size_t smem, cudaStream_t st) {

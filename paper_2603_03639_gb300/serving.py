@@ -10,11 +10,14 @@ own noise seed.  The server
   * admits a request when its context's device footprint fits the memory
     budget next to the contexts already holding work (idle contexts are
     destroyed first, least recently used, when memory is short);
-  * launches every admitted request at once on its context's own CUDA stream,
-    so requests that arrive while others run are admitted as slots and memory
-    free up and their kernels overlap on the device (continuous batching: the
-    block scheduler fills the SMs left free by one request's persistent CTAs
-    with the next request's);
+  * launches every admitted request at once on its context's own CUDA
+    stream, with the trajectory kernel in its pooled form (one CTA per
+    trajectory, work regions from a pool), so requests that arrive while
+    others run are admitted as slots and memory free up and their CTAs start
+    as soon as any running trajectory ends (continuous batching at trajectory
+    granularity); requests of problems that have been quick run on a
+    high-priority stream, so the block scheduler starts their CTAs before the
+    pending CTAs of long requests;
   * completes a request when its stream's event has fired, copying F and the
     gradient back, and records arrival, start and finish times.
 
@@ -60,6 +63,7 @@ class Request:
     substeps: int = 1             # Trotter steps per control bin
     operator: bool = False        # evolve the operator from the identity (gate objective)
     # filled by the server
+    priority: str = ""
     arrival: float = 0.0
     start: float = 0.0
     finish: float = 0.0
@@ -86,34 +90,52 @@ class Request:
 
 
 class _Slot:
-    """A resident context with its stream and device output buffers."""
+    """A resident context with its streams and device output buffers.
+
+    The context launches its trajectories pooled (one CTA per trajectory),
+    so the block scheduler can start other requests' CTAs whenever one of
+    its trajectories ends; the slot owns a high- and a low-priority stream
+    and runs each request on the one its problem's size calls for."""
 
     def __init__(self, req: Request, device):
         import torch
         self.key = req.key
-        self.stream = torch.cuda.Stream(device=device)
+        lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
+        self.streams = (torch.cuda.Stream(device=device, priority=hi), torch.cuda.Stream(device=device, priority=lo))
+        self.stream = self.streams[1]
         self.ctx = Context(req.N, req.K, req.dt, req.chi, req.M, req.C, req.inputs, req.targets,
                            cutoff=req.cutoff, mask=req.mask, stream=self.stream.cuda_stream, **req.form())
+        self.ctx.set_pooled(True)   # other requests' CTAs can start between this one's trajectories
         self.ctx.set_graphs(True)   # each request replays the context's captured evaluation
         self.bytes = req.footprint()
         self.F = torch.zeros(1, dtype=torch.float64, device=device)
         self.g = torch.zeros((req.K, req.C, req.N), dtype=torch.float64, device=device)
-        self.event = torch.cuda.Event()
+        self.ev0 = torch.cuda.Event(enable_timing=True)
+        self.event = torch.cuda.Event(enable_timing=True)
         self.busy: Optional[Request] = None
         self.last_used = 0.0
+        self.service: Optional[float] = None   # shortest device span of this problem's requests (s)
 
-    def launch(self, req: Request):
+    def launch(self, req: Request, high: bool):
         import torch
-        with torch.cuda.stream(self.stream):
+        st = self.streams[0] if high else self.streams[1]
+        if st is not self.stream:
+            self.ctx.set_stream(st.cuda_stream)
+            self.stream = st
+        with torch.cuda.stream(st):
+            self.ev0.record(st)
             self.ctx.set_controls(req.controls)
             self.ctx.sample_noise(req.noise_seed, req.noise_dist, req.noise_scale)
             self.ctx.evaluate_dev(self.F.data_ptr(), self.g.data_ptr() if req.want_grad else 0)
-            self.event.record(self.stream)
+            self.event.record(st)
+        req.priority = "high" if high else "low"
         self.busy = req
 
     def collect(self):
         req = self.busy
         self.ctx.sync()
+        span = self.ev0.elapsed_time(self.event) / 1000.0
+        self.service = span if self.service is None else min(self.service, span)
         req.F = float(self.F.item())
         req.grad = self.g.cpu().numpy().copy() if req.want_grad else None
         self.busy = None
@@ -127,9 +149,14 @@ class Server:
     """Continuous-batching server on one device.
 
     mem_budget: device bytes the resident contexts may hold (default: 60% of
-    the free memory at start); max_inflight: requests on the device at once."""
+    the free memory at start); max_inflight: requests on the device at once;
+    short_s: a request whose problem has been served in at most this many
+    seconds of device time runs on a high-priority stream, so that its CTAs
+    start before the pending CTAs of longer requests (shortest work first at
+    trajectory granularity); a problem not yet measured runs at low priority."""
 
-    def __init__(self, mem_budget: Optional[int] = None, max_inflight: int = 8, device: int = 0):
+    def __init__(self, mem_budget: Optional[int] = None, max_inflight: int = 8, device: int = 0,
+                 short_s: float = 0.1):
         import torch
         self.device = torch.device("cuda", device)
         if mem_budget is None:
@@ -137,6 +164,7 @@ class Server:
             mem_budget = int(0.6 * free)
         self.mem_budget = mem_budget
         self.max_inflight = max_inflight
+        self.short_s = short_s
         self.pending = collections.deque()
         self.slots: list = []
         self.done: list = []
@@ -154,6 +182,16 @@ class Server:
         with self.cv:
             self.pending.append(req)
             self.cv.notify()
+        return req
+
+    def wait(self, req: Request, timeout: float = 600.0) -> Request:
+        """Block until ``req`` (submitted earlier) has finished or failed."""
+        t0 = time.perf_counter()
+        with self.cv:
+            while req.finish == 0.0:
+                if time.perf_counter() - t0 > timeout:
+                    raise TimeoutError("request still pending")
+                self.cv.wait(0.01)
         return req
 
     def drain(self, timeout: float = 600.0):
@@ -211,7 +249,7 @@ class Server:
                 slot = _Slot(req, self.device)
             self.slots.append(slot)
         req.start = time.perf_counter()
-        slot.launch(req)
+        slot.launch(req, high=slot.service is not None and slot.service <= self.short_s)
         self.admitted += 1
         return True
 

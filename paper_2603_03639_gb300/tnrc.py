@@ -22,7 +22,7 @@ EXPORTS = ("tnrc_create", "tnrc_set_controls", "tnrc_sample_noise", "tnrc_set_no
            "tnrc_fidelity_grad", "tnrc_get_overlaps", "tnrc_get_stats", "tnrc_set_controls_dev",
            "tnrc_evaluate_dev", "tnrc_sync", "tnrc_footprint", "tnrc_destroy", "tnrc_status_string",
            "tnrc_fidelity_static", "tnrc_set_graphs", "tnrc_last_error", "tnrc_measure_fp64_peak",
-           "tnrc_measure_dmma_peak")
+           "tnrc_measure_dmma_peak", "tnrc_set_pooled", "tnrc_set_stream")
 
 
 class TNRCError(RuntimeError):
@@ -52,12 +52,13 @@ class Stats(ctypes.Structure):
                 ("hist_len", ctypes.c_int32), ("bond_hist", ctypes.c_int64 * 65),
                 ("discarded_weight", ctypes.c_double), ("last_ms", ctypes.c_double),
                 ("alg_flops", ctypes.c_double), ("traj_ms", ctypes.c_double), ("traj_launches", ctypes.c_int64),
-                ("restarts", ctypes.c_int64), ("phase_cycles", ctypes.c_int64 * 8),
+                ("restarts", ctypes.c_int64), ("phase_cycles", ctypes.c_int64 * 9),
                 ("cap_truncations", ctypes.c_int64), ("min_trunc_gap", ctypes.c_double)]
 
 
 #: trajectory-kernel phases of tnrc_stats.phase_cycles
-PHASES = ("contraction", "jacobi", "truncate", "split", "environments", "gradients", "history", "barriers")
+PHASES = ("contraction", "qr", "truncate", "split", "environments", "gradients", "history", "barriers",
+          "jacobi")
 
 _LIB = None
 
@@ -92,6 +93,10 @@ def lib() -> ctypes.CDLL:
         L.tnrc_last_error.restype = ctypes.c_char_p
         L.tnrc_set_graphs.argtypes = [vp, i32]
         L.tnrc_set_graphs.restype = i32
+        L.tnrc_set_pooled.argtypes = [vp, i32]
+        L.tnrc_set_pooled.restype = i32
+        L.tnrc_set_stream.argtypes = [vp, vp]
+        L.tnrc_set_stream.restype = i32
         L.tnrc_footprint.argtypes = [ctypes.POINTER(Problem)]
         L.tnrc_footprint.restype = ctypes.c_size_t
         L.tnrc_destroy.argtypes = [vp]
@@ -305,6 +310,15 @@ class Context:
 
     def set_graphs(self, enable: bool = True):
         _check(lib().tnrc_set_graphs(self._h, 1 if enable else 0), "tnrc_set_graphs", self._h)
+
+    def set_stream(self, stream: int):
+        """Order later work on another CUDA stream (waits for queued work)."""
+        _check(lib().tnrc_set_stream(self._h, ctypes.c_void_p(stream or None)), "tnrc_set_stream", self._h)
+        self.stream = int(stream or 0)
+
+    def set_pooled(self, enable: bool = True):
+        """One CTA per trajectory with work regions from a pool (see the header)."""
+        _check(lib().tnrc_set_pooled(self._h, 1 if enable else 0), "tnrc_set_pooled", self._h)
 
     def sync(self):
         _check(lib().tnrc_sync(self._h), "tnrc_sync", self._h)

@@ -51,3 +51,51 @@ def test_robust_gate_optimisation_with_the_operator_form():
     assert final.infidelity < runs[0].history[0]
     assert final.validation < 0.1 * base      # the oracle-backed loop reaches about 1/400 here
     assert np.all(np.isfinite(final.u))
+
+
+def test_chain_length_warm_start_through_the_serving_loop():
+    """Sec. II's warm start over the chain length: the robust solution for
+    n = 3 sites, extended to 4, seeds the n = 4 optimisation.  That optimiser
+    and a cold-started one (random controls, as the paper warns against) run
+    at the same time as clients of one serving loop, with equal iteration
+    budgets; the warm start must reach the lower infidelity on 5M fresh
+    samples."""
+    import threading
+    from paper_2603_03639_gb300 import Context, grape
+    from paper_2603_03639_gb300.serving import Request, Server
+    base = synth.WORKLOADS["x8"].replace(K=10, dt=0.1, P=3, chi=4)
+    dJ = 0.1
+
+    def states(n):
+        return base.replace(N=n).states()
+
+    def make(n, M):
+        ins, tgs = states(n)
+        return Context(n, base.K, base.dt, base.chi, M, base.C, ins, tgs, mask=base.replace(N=n).mask())
+
+    u3 = synth.controls(base.K, base.C, 3, 1, 0.5)
+    with make(3, 12) as ctx:
+        r3 = grape.optimise(ctx, u3, (5, 0, dJ), maxiter=30)
+    ins4, tgs4 = states(4)
+    starts = {"warm": grape.extend_controls(r3.u, 4), "cold": synth.controls(base.K, base.C, 4, 1, 0.5)}
+    srv = Server(max_inflight=4)
+    results = {}
+
+    def run(name):
+        tmpl = Request(key="n4", N=4, K=base.K, dt=base.dt, chi=base.chi, M=18, C=base.C, inputs=ins4,
+                       targets=tgs4, controls=starts[name], noise_seed=6, noise_dist=0, noise_scale=dJ,
+                       mask=base.replace(N=4).mask())
+        results[name] = grape.optimise_fn(grape.ServedObjective(srv, tmpl), starts[name], maxiter=30)
+
+    threads = [threading.Thread(target=run, args=(k,)) for k in starts]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    peak = srv.peak_inflight
+    srv.close()
+    assert peak >= 2                     # the two optimisers' requests shared the device
+    for name, r in results.items():
+        r.validation = grape.validate(lambda M: make(4, M), r.u, 18, (20006, 0, dJ))
+    assert results["warm"].validation < results["cold"].validation
+    assert results["warm"].infidelity < results["warm"].history[0]

@@ -338,3 +338,39 @@ def test_graph_replay_equals_plain_launches():
     for (Fa, ga), (Fb, gb) in zip(outs[False], outs[True]):
         assert Fa == Fb and np.array_equal(ga, gb)
     assert outs[True][3][0] == outs[True][0][0]
+
+
+def test_pooled_launch_equals_persistent_launch():
+    """The pooled form (one CTA per trajectory, work regions from a device
+    pool) gives bitwise the persistent form's results, with more trajectories
+    than regions (so regions are handed from CTA to CTA) and with graphs."""
+    import torch
+    w = synth.WORKLOADS["cnot50"].replace(N=12, K=6, chi=16, M=100, P=2)   # 200 trajectories, 152 regions
+    u, mask, J, ins, tgs = case(w)
+    out = {}
+    for pooled in (False, True):
+        ctx = gpu_context(w, ins, tgs, mask, warps=4, ctas_per_sm=1)
+        ctx.set_pooled(pooled)
+        ctx.set_controls(u)
+        ctx.set_noise(J)
+        out[pooled] = ctx.fidelity_grad()
+        ctx.close()
+    assert out[True][0] == out[False][0]
+    assert np.array_equal(out[True][1], out[False][1])
+    side = torch.cuda.Stream()
+    from paper_2603_03639_gb300 import Context
+    ctx = Context(w.N, w.K, w.dt, w.chi, w.M, w.C, ins, tgs, mask=mask, stream=side.cuda_stream, warps=4,
+                  ctas_per_sm=1)
+    ctx.set_pooled(True)
+    ctx.set_graphs(True)
+    ctx.set_noise(J)
+    ud = torch.tensor(u, dtype=torch.float64, device="cuda")
+    F = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g = torch.zeros(u.shape, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    for _ in range(2):
+        ctx.set_controls_dev(ud.data_ptr())
+        ctx.evaluate_dev(F.data_ptr(), g.data_ptr())
+        ctx.sync()
+        assert F.item() == out[False][0] and np.array_equal(g.cpu().numpy(), out[False][1])
+    ctx.close()

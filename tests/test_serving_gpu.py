@@ -71,3 +71,34 @@ def test_request_larger_than_budget_is_refused_and_server_keeps_going():
     errs = [r for r in reqs if r.error]
     assert big in errs
     assert all(r.F is not None for r in reqs if r.footprint() < big.footprint())
+
+
+def test_short_request_overtakes_a_long_one():
+    """Continuous batching at trajectory granularity: a short request that
+    arrives while a long one occupies every SM finishes first -- its CTAs
+    (high-priority stream) start as soon as some of the long request's
+    trajectories end, instead of after the whole long request."""
+    import time
+    from paper_2603_03639_gb300.serving import Request, Server
+    rng = np.random.default_rng(9)
+
+    def req(w, key):
+        ins, tgs = w.states()
+        return Request(key=key, N=w.N, K=w.K, dt=w.dt, chi=w.chi, M=w.M, C=w.C, inputs=ins, targets=tgs,
+                       controls=rng.normal(0, 0.5, size=(w.K, w.C, w.N)), noise_seed=int(rng.integers(1 << 40)),
+                       noise_dist=w.noise_dist, noise_scale=w.noise_scale, want_grad=True, mask=w.mask())
+
+    long_w = synth.WORKLOADS["x50"].replace(M=96)
+    short_w = synth.WORKLOADS["x8"].replace(M=8)
+    srv = Server(max_inflight=4)
+    for w, key in ((long_w, "long"), (short_w, "short")):   # resident and measured
+        srv.submit(req(w, key))
+        srv.drain()
+    big = srv.submit(req(long_w, "long"))
+    time.sleep(0.05)
+    small = srv.submit(req(short_w, "short"))
+    srv.drain()
+    srv.close()
+    assert big.error is None and small.error is None
+    assert small.priority == "high" and big.priority == "low"
+    assert small.finish < big.finish
