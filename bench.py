@@ -606,7 +606,7 @@ def main():
     ap.add_argument("--rates", default="8,32")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--no-serving", action="store_true", help="leave the serving block out of the bench line")
-    ap.add_argument("--serve-rate", type=float, default=32.0)
+    ap.add_argument("--serve-rate", type=float, default=8.0)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--plain", action="store_true",
                     help="plain (one CTA) vs batched launch on a sample of the workload (separate JSON line)")

@@ -128,7 +128,7 @@ extern "C" tnrc_status tnrc_fidelity_static(const tnrc_problem* pb, const tnrc_m
   const int warps = std::max(2, std::min(tnrc::kWarps, maxb));
   const int slab = std::min(1024, d * d * chi * chi);
   const int64_t cc = (int64_t)chi * chi;
-  const int64_t scratch_elems = 4 * (int64_t)d * d * cc;
+  const int64_t scratch_elems = (4 * (int64_t)d * d + d) * cc;   // the same per-warp layout as tnrc_create
   const int64_t env_elems = 2 * (int64_t)(N + 1) * cc;
   const int64_t per_cta = up(L.bytes) + up(warps * scratch_elems * 16) + up(env_elems * 16);
   if (off + per_cta > (int64_t)kStaticBytes) return TNRC_E_TOO_LARGE;

@@ -150,7 +150,9 @@ inline bool make_plan(const tnrc_problem* pb, int n_sm, size_t free_bytes, Plan&
     P.slab_elems = std::max(256, std::min(P.d * P.d * chi * chi, per_warp / 32 * 32));
   }
   const int64_t cc = (int64_t)chi * chi;
-  P.scratch_elems = 4 * (int64_t)P.d * P.d * cc;   // Phi and theta (d chi)^2 each, and more
+  // per warp: Phi (d chi)^2, theta (d chi)^2, then the gradient's three
+  // intermediates (at most (d + 2 d^2) chi^2) past 2 (d chi)^2
+  P.scratch_elems = (4 * (int64_t)P.d * P.d + P.d) * cc;
   P.env_elems = 2 * (int64_t)(N + 1) * cc;
   P.work_stride = (int64_t)(2 + P.nseg + P.seg) * P.L.bytes;
   const int64_t per_cta = P.work_stride + (P.scratch_elems * P.warps + P.env_elems) * 16;

@@ -49,6 +49,8 @@ struct WarpCtx {
   int* order;               // shared, CTA-wide: bonds of the current layer by decreasing cost
   int* next;                // shared, CTA-wide: next entry of `order` to take
   int region;               // the CTA's work region (scratch, environments, slots)
+  volatile int* lready;     // shared: left environments L_0 .. L_lready are built
+  volatile int* rready;     // shared: right environments R_rready .. R_N are built
 };
 
 // Algorithmic flops of one two-site update with theta of m x n (m = 2 Dl,
@@ -68,6 +70,13 @@ __device__ __forceinline__ const LayerGate& layer_rec(const TrajParams& p, int s
   return p.lgates[(size_t)s * p.recs_per_sample + p.layer_off[l] + (b >> 1)];
 }
 
+// Where the two-site update of a theta with n_theta elements keeps theta:
+// the warp's shared slab when it fits, else its global scratch past Phi's
+// room.
+__device__ __forceinline__ double2* theta_home(const TrajParams& p, int kDD, int n_theta, WarpCtx& w) {
+  return (n_theta <= p.slab_elems) ? w.slab : (w.scratch + (size_t)kDD * p.chi * p.chi);
+}
+
 // ---------------------------------------------------------------------------
 // Physical dimension kD: 2 for qubit states; 4 for operators written as
 // vectors (site index s = 2 out + in, the MPO of Sec. II), where the 4x4 gate
@@ -82,7 +91,7 @@ __device__ __forceinline__ const LayerGate& layer_rec(const TrajParams& p, int s
 // ---------------------------------------------------------------------------
 template <int kD>
 __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char* slot, int b, const double2* G,
-                                bool adjoint, bool record, bool count, WarpCtx& w) {
+                                bool adjoint, bool record, bool count, WarpCtx& w, const double2* pre = nullptr) {
   constexpr int kI = kD / 2;
   const int lane = w.lane;
   const int chi = p.chi;
@@ -95,7 +104,7 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   double2* A = sites + Y.site_off[b];
   double2* Bt = sites + Y.site_off[b + 1];
   // theta (then R^dagger) and Phi in the warp's shared slab when they fit
-  double2* T = (m * n <= p.slab_elems) ? w.slab : (w.scratch + (size_t)kD * kD * chi * chi);
+  double2* T = theta_home(p, kD * kD, m * n, w);
   double2* Phi = (2 * m * n <= p.slab_elems) ? w.slab + m * n : w.scratch;
 
   double2 g[16];
@@ -105,25 +114,33 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
     for (int c = 0; c < 4; ++c) g[r * 4 + c] = adjoint ? cconj(G[c * 4 + r]) : G[r * 4 + c];
 
   // Phase 1: Phi = G (B_b B_{b+1}) and theta, both row-major: row (al s1), column (s2 ga).
+  // With `pre` the product B_b B_{b+1} is given ([Dl][kD^2][Dr], the layout
+  // of theta itself, so pre may be T: each item reads and writes only its own
+  // kD^2 entries).
   TNRC_TIC(t_c);
   double fro = 0.0;
   for (int it = lane; it < Dl * Dr; it += 32) {
     const int al = it / Dr, ga = it - al * Dr;
     double2 acc[kD * kD];   // (B_b B_{b+1})[al][s1][s2][ga] at s1 kD + s2
+    if (pre) {
 #pragma unroll
-    for (int q = 0; q < kD * kD; ++q) acc[q] = make_double2(0.0, 0.0);
-    const double2* ap = A + (size_t)(al * kD) * Dc;
-    for (int be = 0; be < Dc; ++be) {
-      double2 av[kD], bv[kD];
+      for (int q = 0; q < kD * kD; ++q) acc[q] = pre[((size_t)al * kD * kD + q) * Dr + ga];
+    } else {
 #pragma unroll
-      for (int q = 0; q < kD; ++q) {
-        av[q] = ap[(size_t)q * Dc + be];
-        bv[q] = Bt[(size_t)(be * kD + q) * Dr + ga];
+      for (int q = 0; q < kD * kD; ++q) acc[q] = make_double2(0.0, 0.0);
+      const double2* ap = A + (size_t)(al * kD) * Dc;
+      for (int be = 0; be < Dc; ++be) {
+        double2 av[kD], bv[kD];
+#pragma unroll
+        for (int q = 0; q < kD; ++q) {
+          av[q] = ap[(size_t)q * Dc + be];
+          bv[q] = Bt[(size_t)(be * kD + q) * Dr + ga];
+        }
+#pragma unroll
+        for (int q1 = 0; q1 < kD; ++q1)
+#pragma unroll
+          for (int q2 = 0; q2 < kD; ++q2) cfma(acc[q1 * kD + q2], av[q1], bv[q2]);
       }
-#pragma unroll
-      for (int q1 = 0; q1 < kD; ++q1)
-#pragma unroll
-        for (int q2 = 0; q2 < kD; ++q2) cfma(acc[q1 * kD + q2], av[q1], bv[q2]);
     }
     const double ll = (b > 0) ? lam[(size_t)(b - 1) * lstride + al] : 1.0;
 #pragma unroll
@@ -356,16 +373,45 @@ __device__ double2 warp_overlap(const TrajParams& p, const Lay& Yt, const unsign
   return E0[0];
 }
 
+// Cost of a two-site update with theta of (2 Dl) x (2 Dr): the Jacobi work
+// grows as m n min(m, n).
+__device__ __forceinline__ long long update_cost(int Dl, int Dr) {
+  const long long m = 2 * Dl, n = 2 * Dr;
+  return m * n * (m < n ? m : n);
+}
+
+// One warp: the bonds of parity `parity` in decreasing order of update cost
+// into w.order, and the shared counter reset.
+__device__ inline void order_layer(const TrajParams& p, const int* D, int parity, WarpCtx& w) {
+  const int nb = (p.N - 1 - parity + 1) / 2;
+  const int lane = w.lane;
+  for (int j = lane; j < nb; j += 32) {
+    const long long cj = update_cost(D[parity + 2 * j], D[parity + 2 * j + 2]);
+    int rk = 0;
+    for (int i = 0; i < nb; ++i) {
+      const long long ci = update_cost(D[parity + 2 * i], D[parity + 2 * i + 2]);
+      rk += (ci > cj || (ci == cj && i < j)) ? 1 : 0;
+    }
+    w.order[rk] = parity + 2 * j;
+  }
+  if (lane == 0) *w.next = 0;
+}
+
 // ---------------------------------------------------------------------------
-// Gradient of one layer: environments, mixed two-site densities rho, and
-// dO/du = tr(Q_u rho) for every control u of every gate in the layer, added
-// to the trajectory's gradient row as 2 Re(conj(O) dO/du).
+// Gradient of one layer (App. A), split so that each bond's gradient and its
+// costate update run back to back on one warp:
+//   layer_envs    left/right environments of <c|.|a> for the layer (warps 0
+//                 and 1) and the bonds ordered by cost (the last warp);
+//   bond_gradient the mixed two-site density rho of bond b and dO/du =
+//                 tr(Q_u rho) for every control u of its gate, added to the
+//                 trajectory's gradient row as 2 Re(conj(O) dO/du); it leaves
+//                 the costate's two-site product c_b c_{b+1} where the costate
+//                 update of the bond takes theta, which then skips its own
+//                 contraction.
 // ---------------------------------------------------------------------------
 template <int kD>
-__device__ void layer_gradient(const TrajParams& p, const Lay& Y, const unsigned char* cslot, const StateView av,
-                               int s, int l, double2 wO, double* gsp_row, WarpCtx& w, int warp) {
-  constexpr int kDD = kD * kD, kI = kD / 2;
-  const int parity = layer_parity(p, l);
+__device__ void layer_envs(const TrajParams& p, const Lay& Y, const unsigned char* cslot, const StateView av,
+                           WarpCtx& w, int warp) {
   const int N = p.N, chi = p.chi;
   const size_t cc = (size_t)chi * chi;
   const int* Dc = slot_dims(cslot);
@@ -378,131 +424,173 @@ __device__ void layer_gradient(const TrajParams& p, const Lay& Y, const unsigned
   double2* Rbuf = Lbuf + (size_t)(N + 1) * cc;
   const int lane = w.lane;
 
-  // left environments L_i (sites < i) for i <= N-2, right R_i (sites >= i) for i >= 2
+  // left environments L_i (sites < i) for i <= N-2, right R_i (sites >= i)
+  // for i >= 2; each step publishes its progress (after a block-scope fence)
+  // for the warps already working on bonds
   TNRC_TIC(t_e);
   if (warp == 0) {
-    if (lane == 0) Lbuf[0] = make_double2(1.0, 0.0);
-    __syncwarp();
     for (int i = 0; i + 1 <= N - 2; ++i) {
       // the step's intermediate (Dc[i] x kD Da[i+1]) in the warp's shared slab when it fits
       double2* tmp = (Dc[i] * kD * Da[i + 1] <= p.slab_elems) ? w.slab : w.scratch;
       env_left_step<kD>(Lbuf + i * cc, Dc[i], Da[i], cs + so[i], Dc[i + 1], as + ao[i], Da[i + 1],
                         tmp, Lbuf + (i + 1) * cc, lane);
       w.alg += 8ull * kD * Da[i + 1] * (unsigned long long)(Dc[i] * Da[i] + Dc[i + 1] * Dc[i]);
+      __syncwarp();
+      __threadfence_block();
+      if (lane == 0) *w.lready = i + 1;
     }
   } else if (warp == 1) {
-    if (lane == 0) Rbuf[(size_t)N * cc] = make_double2(1.0, 0.0);
-    __syncwarp();
     for (int i = N - 1; i >= 2; --i) {
       double2* tmp = (Dc[i + 1] * kD * Da[i] <= p.slab_elems) ? w.slab : w.scratch;
       env_right_step<kD>(Rbuf + (size_t)(i + 1) * cc, Dc[i + 1], Da[i + 1], cs + so[i], Dc[i],
                          as + ao[i], Da[i], tmp, Rbuf + (size_t)i * cc, lane);
       w.alg += 8ull * kD * Da[i] * (unsigned long long)(Dc[i + 1] * Da[i + 1] + Dc[i] * Dc[i + 1]);
+      __syncwarp();
+      __threadfence_block();
+      if (lane == 0) *w.rready = i;
     }
   }
-  __syncthreads();
   TNRC_TOC(w, 4, t_e);
-  TNRC_TIC(t_g);
+}
 
-  const int nb = (N - 1 - parity + 1) / 2;
-  for (int j = warp; j < nb; j += p.warps) {
-    const int b = parity + 2 * j;
-    const int dcl = Dc[b], dcm = Dc[b + 1], dcr = Dc[b + 2];
-    const int dal = Da[b], dam = Da[b + 1], dar = Da[b + 2];
-    const double2* L = Lbuf + (size_t)b * cc;
-    const double2* R = Rbuf + (size_t)(b + 2) * cc;
-    const double2* a0 = as + ao[b];
-    const double2* a1 = as + ao[b + 1];
-    const double2* c0 = cs + so[b];
-    const double2* c1 = cs + so[b + 1];
-    w.alg += 8ull * dcl * (kD * dam * dal + kDD * dcr * dcm + kDD * dar * dam + kDD * dcr * dar +
-                           (unsigned long long)kDD * kDD * dcr) + 2048ull;
-    // the four intermediates packed at their actual sizes, in the warp's shared
-    // slab when they fit (the slab is idle outside the two-site update)
-    const int n1 = dcl * kD * dam, n2 = dcl * kDD * dar, n3 = dcl * kDD * dcr;
-    double2* U1 = (n1 + n2 + 2 * n3 <= p.slab_elems) ? w.slab : w.scratch;   // [dcl][kD][dam]
-    double2* U2 = U1 + n1;                          // [dcl][kD^2][dar]
-    double2* U3 = U2 + n2;                          // [dcl][kD^2][dcr]
-    double2* Wc = U3 + n3;                          // [dcl][kD^2][dcr]
-    for (int it = lane; it < dcl * kD * dam; it += 32) {
-      const int be = it / (kD * dam), rest = it - be * kD * dam;
-      double2 acc = make_double2(0.0, 0.0);
-      for (int al = 0; al < dal; ++al) cfma(acc, L[be * dal + al], a0[(size_t)al * kD * dam + rest]);
-      U1[it] = acc;
+// Waits (bounded) until both environment sweeps are past sites b and b+1:
+// bond b's gradient then has L_b and R_{b+2}, and its costate update may
+// rewrite the two sites, which neither sweep reads again.  Gives up after
+// kEnvWaitCycles SM cycles (a few seconds, far beyond any sweep) with the
+// timeout status set.
+__device__ inline void wait_envs(const TrajParams& p, int b, WarpCtx& w) {
+  const int lneed = min(b + 2, p.N - 2), rneed = max(b, 2);
+  int ok = 1;
+  if (w.lane == 0) {
+    const long long t0 = clock64();
+    while (*w.lready < lneed || *w.rready > rneed) {
+      if (clock64() - t0 > kEnvWaitCycles) {
+        ok = 0;
+        break;
+      }
+      __nanosleep(128);
     }
-    for (int it = lane; it < dcl * kDD * dcr; it += 32) {
-      const int be = it / (kDD * dcr), rest = it - be * kDD * dcr;
-      const int ss = rest / dcr, b2 = rest - ss * dcr;
-      const int s1 = ss / kD, s2 = ss % kD;
-      double2 acc = make_double2(0.0, 0.0);
-      for (int b1 = 0; b1 < dcm; ++b1)
-        cfma(acc, c0[(size_t)be * kD * dcm + s1 * dcm + b1], c1[(size_t)b1 * kD * dcr + s2 * dcr + b2]);
-      Wc[it] = acc;
-    }
-    __syncwarp();
-    for (int it = lane; it < dcl * kDD * dar; it += 32) {
-      const int be = it / (kDD * dar), rest = it - be * kDD * dar;
-      const int ss = rest / dar, a2 = rest - ss * dar;
-      const int s1 = ss / kD, s2 = ss % kD;
-      double2 acc = make_double2(0.0, 0.0);
-      for (int a1i = 0; a1i < dam; ++a1i)
-        cfma(acc, U1[(size_t)be * kD * dam + s1 * dam + a1i], a1[(size_t)a1i * kD * dar + s2 * dar + a2]);
-      U2[it] = acc;
-    }
-    __syncwarp();
-    for (int it = lane; it < dcl * kDD * dcr; it += 32) {
-      const int be = it / (kDD * dcr), rest = it - be * kDD * dcr;
-      const int ss = rest / dcr, b2 = rest - ss * dcr;
-      double2 acc = make_double2(0.0, 0.0);
-      const double2* u2 = U2 + (size_t)be * kDD * dar + ss * dar;
-      const double2* rr = R + (size_t)b2 * dar;
-      for (int a2 = 0; a2 < dar; ++a2) cfma(acc, u2[a2], rr[a2]);
-      U3[it] = acc;
-    }
-    __syncwarp();
-    // rho[o'][o] = sum_{i1,i2} sum_{be,b2} U3[be][s'][b2] conj(Wc[be][s][b2]) over the
-    // two-site out indices o (the in indices, if any, traced out: the gate acts
-    // as Q (x) I); lane = (o', o) pair, 16 lanes x 2 halves
-    double2* rho = w.small;
-    {
-      const int o = lane & 15, half = lane >> 4;
-      const int op = o >> 2, oq = o & 3;
-      double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int i1 = 0; i1 < kI; ++i1)
-#pragma unroll
-        for (int i2 = 0; i2 < kI; ++i2) {
-          const int sp = ((op >> 1) * kI + i1) * kD + (op & 1) * kI + i2;
-          const int sq = ((oq >> 1) * kI + i1) * kD + (oq & 1) * kI + i2;
-          for (int be = half; be < dcl; be += 2) {
-            const double2* u = U3 + (size_t)be * kDD * dcr + sp * dcr;
-            const double2* wv = Wc + (size_t)be * kDD * dcr + sq * dcr;
-            for (int b2 = 0; b2 < dcr; ++b2) cfmac(acc, wv[b2], u[b2]);
-          }
-        }
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
-      if (lane < 16) rho[o] = acc;
-    }
-    __syncwarp();
-    // dO/du_q = tr(Q_q rho) = sum_ij Q_q[i][j] rho[j][i]: lane q takes control q
-    const LayerGate& lg = layer_rec(p, s, l, b);
-    const int nq = lg.nq;
-    if (lane < nq) {
-      const double2* Q = lg.Q[lane];
-      double2 v = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) cfma(v, Q[i * 4 + j], rho[j * 4 + i]);
-      // explicit fma: this function is inlined into both history modes, which
-      // must round identically
-      gsp_row[lg.slot[lane]] += 2.0 * fma(wO.x, v.x, wO.y * v.y);
-    }
-    __syncwarp();
   }
+  __syncwarp();
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok && w.lane == 0) atomicOr(p.status, kStatusTimeout);
+  __threadfence_block();
+}
+
+template <int kD>
+__device__ void bond_gradient(const TrajParams& p, const Lay& Y, const unsigned char* cslot, const StateView av,
+                              int s, int l, int b, double2 wO, double* gsp_row, WarpCtx& w, double2* Wc) {
+  constexpr int kDD = kD * kD, kI = kD / 2;
+  const int N = p.N, chi = p.chi;
+  const size_t cc = (size_t)chi * chi;
+  const int* Dc = slot_dims(cslot);
+  const int* Da = av.D;
+  const double2* cs = slot_sites(cslot, Y.L);
+  const double2* as = av.sites;
+  const int* so = Y.site_off;
+  const int* ao = av.off;
+  const double2* Lbuf = p.env_scratch + (size_t)w.region * 2 * (N + 1) * cc;
+  const double2* Rbuf = Lbuf + (size_t)(N + 1) * cc;
+  const int lane = w.lane;
+  TNRC_TIC(t_g);
+  const int dcl = Dc[b], dcm = Dc[b + 1], dcr = Dc[b + 2];
+  const int dal = Da[b], dam = Da[b + 1], dar = Da[b + 2];
+  const double2* L = Lbuf + (size_t)b * cc;
+  const double2* R = Rbuf + (size_t)(b + 2) * cc;
+  const double2* a0 = as + ao[b];
+  const double2* a1 = as + ao[b + 1];
+  const double2* c0 = cs + so[b];
+  const double2* c1 = cs + so[b + 1];
+  // the costate product c_b c_{b+1} is shared with the bond's costate update
+  // (counted there)
+  w.alg += 8ull * dcl * (kD * dam * dal + kDD * dar * dam + kDD * dcr * dar +
+                         (unsigned long long)kDD * kDD * dcr) + 2048ull;
+  // Wc = c_b c_{b+1} [dcl][kD^2][dcr] at Wc (theta's home); the other three
+  // intermediates packed at their actual sizes after it in the warp's shared
+  // slab when everything fits, else in its global scratch past theta's room
+  const int n1 = dcl * kD * dam, n2 = dcl * kDD * dar, n3 = dcl * kDD * dcr;
+  double2* U1 = (Wc == w.slab && n3 + n1 + n2 + n3 <= p.slab_elems)
+                    ? w.slab + n3
+                    : w.scratch + (size_t)2 * kDD * chi * chi;   // [dcl][kD][dam]
+  double2* U2 = U1 + n1;                          // [dcl][kD^2][dar]
+  double2* U3 = U2 + n2;                          // [dcl][kD^2][dcr]
+  for (int it = lane; it < dcl * kD * dam; it += 32) {
+    const int be = it / (kD * dam), rest = it - be * kD * dam;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int al = 0; al < dal; ++al) cfma(acc, L[be * dal + al], a0[(size_t)al * kD * dam + rest]);
+    U1[it] = acc;
+  }
+  for (int it = lane; it < dcl * kDD * dcr; it += 32) {
+    const int be = it / (kDD * dcr), rest = it - be * kDD * dcr;
+    const int ss = rest / dcr, b2 = rest - ss * dcr;
+    const int s1 = ss / kD, s2 = ss % kD;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int b1 = 0; b1 < dcm; ++b1)
+      cfma(acc, c0[(size_t)be * kD * dcm + s1 * dcm + b1], c1[(size_t)b1 * kD * dcr + s2 * dcr + b2]);
+    Wc[it] = acc;
+  }
+  __syncwarp();
+  for (int it = lane; it < dcl * kDD * dar; it += 32) {
+    const int be = it / (kDD * dar), rest = it - be * kDD * dar;
+    const int ss = rest / dar, a2 = rest - ss * dar;
+    const int s1 = ss / kD, s2 = ss % kD;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int a1i = 0; a1i < dam; ++a1i)
+      cfma(acc, U1[(size_t)be * kD * dam + s1 * dam + a1i], a1[(size_t)a1i * kD * dar + s2 * dar + a2]);
+    U2[it] = acc;
+  }
+  __syncwarp();
+  for (int it = lane; it < dcl * kDD * dcr; it += 32) {
+    const int be = it / (kDD * dcr), rest = it - be * kDD * dcr;
+    const int ss = rest / dcr, b2 = rest - ss * dcr;
+    double2 acc = make_double2(0.0, 0.0);
+    const double2* u2 = U2 + (size_t)be * kDD * dar + ss * dar;
+    const double2* rr = R + (size_t)b2 * dar;
+    for (int a2 = 0; a2 < dar; ++a2) cfma(acc, u2[a2], rr[a2]);
+    U3[it] = acc;
+  }
+  __syncwarp();
+  // rho[o'][o] = sum_{i1,i2} sum_{be,b2} U3[be][s'][b2] conj(Wc[be][s][b2]) over the
+  // two-site out indices o (the in indices, if any, traced out: the gate acts
+  // as Q (x) I); lane = (o', o) pair, 16 lanes x 2 halves
+  double2* rho = w.small;
+  {
+    const int o = lane & 15, half = lane >> 4;
+    const int op = o >> 2, oq = o & 3;
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int i1 = 0; i1 < kI; ++i1)
+#pragma unroll
+      for (int i2 = 0; i2 < kI; ++i2) {
+        const int sp = ((op >> 1) * kI + i1) * kD + (op & 1) * kI + i2;
+        const int sq = ((oq >> 1) * kI + i1) * kD + (oq & 1) * kI + i2;
+        for (int be = half; be < dcl; be += 2) {
+          const double2* u = U3 + (size_t)be * kDD * dcr + sp * dcr;
+          const double2* wv = Wc + (size_t)be * kDD * dcr + sq * dcr;
+          for (int b2 = 0; b2 < dcr; ++b2) cfmac(acc, wv[b2], u[b2]);
+        }
+      }
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
+    if (lane < 16) rho[o] = acc;
+  }
+  __syncwarp();
+  // dO/du_q = tr(Q_q rho) = sum_ij Q_q[i][j] rho[j][i]: lane q takes control q
+  const LayerGate& lg = layer_rec(p, s, l, b);
+  const int nq = lg.nq;
+  if (lane < nq) {
+    const double2* Q = lg.Q[lane];
+    double2 v = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cfma(v, Q[i * 4 + j], rho[j * 4 + i]);
+    // explicit fma: this function is inlined into both history modes, which
+    // must round identically
+    gsp_row[lg.slot[lane]] += 2.0 * fma(wO.x, v.x, wO.y * v.y);
+  }
+  __syncwarp();
   TNRC_TOC(w, 5, t_g);
-  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -537,13 +625,6 @@ __device__ int copy_slot(const TrajParams& p, const Lay& Ys, const unsigned char
   return 0;
 }
 
-// Cost of a two-site update with theta of (2 Dl) x (2 Dr): the Jacobi work
-// grows as m n min(m, n).
-__device__ __forceinline__ long long update_cost(int Dl, int Dr) {
-  const long long m = 2 * Dl, n = 2 * Dr;
-  return m * n * (m < n ? m : n);
-}
-
 // All bonds of truncated layer l.  The warps take bonds from a shared counter
 // in decreasing order of cost (largest SVD first), so that they reach the
 // layer barrier together; a bond's result does not depend on which warp
@@ -554,19 +635,7 @@ __device__ void apply_layer(const TrajParams& p, const Lay& Y, unsigned char* sl
   const int parity = layer_parity(p, l);
   const int nb = (p.N - 1 - parity + 1) / 2;
   const int lane = w.lane;
-  if (warp == 0) {
-    const int* D = slot_dims(slot);
-    for (int j = lane; j < nb; j += 32) {
-      const long long cj = update_cost(D[parity + 2 * j], D[parity + 2 * j + 2]);
-      int rk = 0;
-      for (int i = 0; i < nb; ++i) {
-        const long long ci = update_cost(D[parity + 2 * i], D[parity + 2 * i + 2]);
-        rk += (ci > cj || (ci == cj && i < j)) ? 1 : 0;
-      }
-      w.order[rk] = parity + 2 * j;
-    }
-    if (lane == 0) *w.next = 0;
-  }
+  if (warp == 0) order_layer(p, slot_dims(slot), parity, w);
   __syncthreads();
   for (;;) {
     int j = 0;
@@ -575,6 +644,51 @@ __device__ void apply_layer(const TrajParams& p, const Lay& Y, unsigned char* sl
     if (j >= nb) break;
     const int b = w.order[j];
     two_site_update<kD>(p, Y, slot, b, layer_rec(p, s, l, b).G, adjoint, record, count, w);
+  }
+  TNRC_TIC(t_b);
+  __syncthreads();
+  TNRC_TOC(w, 7, t_b);
+}
+
+// One layer of the costate sweep (App. A): the environments of <c_l|.|a_l>,
+// and every bond of layer l -- largest first from the shared counter -- its
+// gradient and at once its costate update c_{l-1} = G^dag c_l, which reuses
+// the product c_b c_{b+1} the gradient formed.  Warps 0 and 1 build the left
+// and right environments; the other warps start on a bond as soon as both
+// sweeps are past its two sites (the middle bonds, the largest, come free
+// first), and warps 0 and 1 join when their sweeps end.  A bond's gradient
+// reads only its own two costate sites and the environments; its update
+// rewrites those two sites, which no other bond of the layer and neither
+// sweep touches afterwards.
+template <int kD>
+__device__ void costate_layer(const TrajParams& p, const Lay& Y, unsigned char* cslot, const StateView av, int s,
+                              int l, double2 wO, double* gsp_row, WarpCtx& w, int warp) {
+  constexpr int kDD = kD * kD;
+  const int parity = layer_parity(p, l);
+  const int nb = (p.N - 1 - parity + 1) / 2;
+  const int lane = w.lane;
+  const int* Dc = slot_dims(cslot);
+  const size_t cc = (size_t)p.chi * p.chi;
+  if (warp == p.warps - 1) order_layer(p, Dc, parity, w);
+  if (lane == 0 && warp == 0) {
+    double2* Lbuf = p.env_scratch + (size_t)w.region * 2 * (p.N + 1) * cc;
+    Lbuf[0] = make_double2(1.0, 0.0);
+    Lbuf[(size_t)(2 * p.N + 1) * cc] = make_double2(1.0, 0.0);   // R_N
+    *w.lready = 0;
+    *w.rready = p.N;
+  }
+  __syncthreads();
+  layer_envs<kD>(p, Y, cslot, av, w, warp);
+  for (;;) {
+    int j = 0;
+    if (lane == 0) j = atomicAdd(w.next, 1);
+    j = __shfl_sync(0xffffffffu, j, 0);
+    if (j >= nb) break;
+    const int b = w.order[j];
+    wait_envs(p, b, w);
+    double2* th = theta_home(p, kDD, kDD * Dc[b] * Dc[b + 2], w);
+    bond_gradient<kD>(p, Y, cslot, av, s, l, b, wO, gsp_row, w, th);
+    two_site_update<kD>(p, Y, cslot, b, layer_rec(p, s, l, b).G, true, false, true, w, th);
   }
   TNRC_TIC(t_b);
   __syncthreads();
@@ -657,10 +771,8 @@ __device__ int run_trajectory(const TrajParams& p, bool packed, unsigned char* b
   for (int i = threadIdx.x; i < KCN; i += blockDim.x) grow[i] = 0.0;
   copy_slot<kD>(p, Y, tg, Y, c_slot);
   if (packed) {
-    for (int l = L - 1; l >= 0; --l) {
-      layer_gradient<kD>(p, Y, c_slot, packed_view(harena + hpos[l], p.N), s, l, O, grow, w, warp);
-      apply_layer<kD>(p, Y, c_slot, s, l, true, false, true, w, warp);
-    }
+    for (int l = L - 1; l >= 0; --l)
+      costate_layer<kD>(p, Y, c_slot, packed_view(harena + hpos[l], p.N), s, l, O, grow, w, warp);
     return 0;
   }
   for (int q = Y.nseg - 1; q >= 0; --q) {
@@ -673,10 +785,8 @@ __device__ int run_trajectory(const TrajParams& p, bool packed, unsigned char* b
         copy_slot<kD>(p, Y, ck, Y, segs + (size_t)(l - l0) * sb);
       }
     }
-    for (int l = l1 - 1; l >= l0; --l) {
-      layer_gradient<kD>(p, Y, c_slot, slot_view(segs + (size_t)(l - l0) * sb, Y), s, l, O, grow, w, warp);
-      apply_layer<kD>(p, Y, c_slot, s, l, true, false, true, w, warp);
-    }
+    for (int l = l1 - 1; l >= l0; --l)
+      costate_layer<kD>(p, Y, c_slot, slot_view(segs + (size_t)(l - l0) * sb, Y), s, l, O, grow, w, warp);
   }
   return 0;
 }
@@ -694,6 +804,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) traj_kernel(TrajParam
   __shared__ int s_order[128];
   __shared__ int s_next;
   __shared__ int s_region;
+  __shared__ int s_lready, s_rready;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   double2* slabs = reinterpret_cast<double2*>(smem_raw);
@@ -746,6 +857,8 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) traj_kernel(TrajParam
   for (int i = 0; i < kNumPhases; ++i) w.ph[i] = 0;
   w.order = s_order;
   w.next = &s_next;
+  w.lready = &s_lready;
+  w.rready = &s_rready;
   unsigned char* base = p.work + (size_t)region * p.work_stride;
 
   for (int iter = 0;; ++iter) {

@@ -17,7 +17,8 @@ own noise seed.  The server
     as soon as any running trajectory ends (continuous batching at trajectory
     granularity); requests of problems that have been quick run on a
     high-priority stream, so the block scheduler starts their CTAs before the
-    pending CTAs of long requests;
+    pending CTAs of long requests, and when admission is full the pending
+    request with the shortest measured work is admitted first;
   * completes a request when its stream's event has fired, copying F and the
     gradient back, and records arrival, start and finish times.
 
@@ -222,6 +223,23 @@ class Server:
             pass
         self.slots.remove(slot)
 
+    def _service(self, key):
+        """Shortest device span measured for this problem (s), or None."""
+        known = [s.service for s in self.slots if s.key == key and s.service is not None]
+        return min(known) if known else None
+
+    def _next_pending(self) -> Request:
+        """The pending request to admit next: the one whose problem has the
+        shortest measured service time; unmeasured problems after measured
+        ones; arrival order among equals."""
+        best, best_t = None, None
+        for r in self.pending:
+            t = self._service(r.key)
+            t = float("inf") if t is None else t
+            if best is None or t < best_t:
+                best, best_t = r, t
+        return best
+
     def _held(self):
         return sum(s.bytes for s in self.slots)
 
@@ -273,13 +291,15 @@ class Server:
                         req.finish = time.perf_counter()
                         s.last_used = req.finish
                         self.done.append(req)
-                # admit in arrival order while slots and memory allow
+                # admit while slots and memory allow, shortest known work first
+                # (arrival order among equals): a short request does not wait
+                # behind long ones for admission either
                 inflight = sum(1 for s in self.slots if s.busy is not None)
                 while self.pending and inflight < self.max_inflight:
+                    req = self._next_pending()
                     try:
-                        admitted = self._admit(self.pending[0])
+                        admitted = self._admit(req)
                     except Exception as e:  # creation or launch failed: fail this request only
-                        req = self.pending[0]
                         req.error = "admission failed: %s" % e
                         req.finish = time.perf_counter()
                         self.done.append(req)
@@ -289,7 +309,10 @@ class Server:
                         admitted = True
                     if not admitted:
                         break
-                    self.pending.popleft()
+                    for i, r in enumerate(self.pending):   # by identity: requests hold arrays
+                        if r is req:
+                            del self.pending[i]
+                            break
                     inflight = sum(1 for s in self.slots if s.busy is not None)
                 self.peak_inflight = max(self.peak_inflight, inflight)
                 self.cv.notify_all()
