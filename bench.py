@@ -554,11 +554,16 @@ def serving_arm(args):
 
 
 def plain_arm(args, w):
-    """Plain vs batched on the same sample: the trajectory kernel with one CTA
-    (one trajectory at a time, no graph) against the persistent launch over
-    all SMs, both through tnrc_fidelity_grad, on the workload cut to
-    `--plain-samples` noise samples (all P inputs, all K slices).  Prints one
-    JSON line; the headline number is gpu_arm's."""
+    """Plain vs batched on the same sample of the workload (`--plain-samples`
+    noise samples, all P inputs and K slices), both through the C ABI on one
+    context, each timed over `--steps` repeats after a warm-up:
+      batched   the persistent launch over all SMs (the headline form);
+      plain     tnrc_fidelity_grad_plain: one trajectory at a time, one launch
+                per step, the layer's bonds spread over CTAs -- the whole GPU
+                for one trajectory;
+      one_cta   the persistent kernel with a single CTA (one trajectory at a
+                time on one SM).
+    Prints one JSON line; every form's F and gradient must agree bitwise."""
     import torch
 
     from paper_2603_03639_gb300 import Context, autotune
@@ -566,30 +571,41 @@ def plain_arm(args, w):
     ws = w.replace(M=args.plain_samples)
     ins, tgs = ws.states()
     tuned = autotune.lookup(w.N, w.K, w.chi, w.M, w.P, w.C, grad=True, operator=w.operator)
-    out = {}
-    for mode in ("batched", "plain"):
-        if mode == "plain":
-            os.environ["TNRC_GRID"] = "1"
-        try:
-            ctx = Context(ws.N, ws.K, ws.dt, ws.chi, ws.M, ws.C, ins, tgs, cutoff=ws.sv_cutoff, mask=ws.mask(),
-                          warps=tuned[0], ctas_per_sm=tuned[1], **form_kwargs(ws))
-        finally:
-            os.environ.pop("TNRC_GRID", None)
-        ctx.set_controls(ws.controls())
-        ctx.sample_noise(ws.seed_J, ws.noise_dist, ws.noise_scale)
-        ctx.fidelity_grad()                       # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        F, _ = ctx.fidelity_grad()
-        secs = time.perf_counter() - t0
-        out[mode] = {"value": ws.slice_steps / secs, "s_per_eval": secs, "F": float(F)}
-        ctx.close()
-    line = {"metric": "plain (one CTA, one trajectory at a time) vs batched persistent launch", "unit": UNIT,
+    out, ref = {}, None
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for mode in ("batched", "plain", "one_cta"):
+            if mode == "one_cta":
+                os.environ["TNRC_GRID"] = "1"
+            try:
+                ctx = Context(ws.N, ws.K, ws.dt, ws.chi, ws.M, ws.C, ins, tgs, cutoff=ws.sv_cutoff,
+                              mask=ws.mask(), warps=tuned[0], ctas_per_sm=tuned[1], **form_kwargs(ws))
+            finally:
+                os.environ.pop("TNRC_GRID", None)
+            ctx.set_controls(ws.controls())
+            ctx.sample_noise(ws.seed_J, ws.noise_dist, ws.noise_scale)
+            run = ctx.fidelity_grad_plain if mode == "plain" else ctx.fidelity_grad
+            run()                                  # warm-up
+            torch.cuda.synchronize()
+            reps = 1 if mode == "one_cta" else max(1, args.steps)
+            secs = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                F, g = run()
+                secs.append(time.perf_counter() - t0)
+            sec = statistics.median(secs)
+            out[mode] = {"value": ws.slice_steps / sec, "s_per_eval": sec, "repeats": reps, "F": float(F)}
+            if ref is None:
+                ref = (F, g)
+            out[mode]["identical_to_batched"] = bool(F == ref[0] and np.array_equal(g, ref[1]))
+            ctx.close()
+    line = {"metric": "batched persistent launch vs plain one-trajectory-at-a-time GPU paths", "unit": UNIT,
             "workload": w.name, "sample": "M=%d noise samples x P=%d inputs x K=%d slices, fwd+adjoint"
-            % (ws.M, ws.P, ws.K), "batched": out["batched"], "plain": out["plain"],
-            "speedup": out["batched"]["value"] / out["plain"]["value"],
-            "results_identical": bool(out["batched"]["F"] == out["plain"]["F"]),
-            "launch_shape": {"warps_per_cta": tuned[0] or "default", "ctas_per_sm": tuned[1] or 1}}
+            % (ws.M, ws.P, ws.K), "batched": out["batched"], "plain": out["plain"], "one_cta": out["one_cta"],
+            "speedup_vs_plain": out["batched"]["value"] / out["plain"]["value"],
+            "speedup_vs_one_cta": out["batched"]["value"] / out["one_cta"]["value"],
+            "results_identical": all(v["identical_to_batched"] for v in out.values()),
+            "launch_shape": {"warps_per_cta": tuned[0] or "default", "ctas_per_sm": tuned[1] or 1},
+            "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 

@@ -210,6 +210,19 @@ tnrc_status tnrc_evaluate_dev(tnrc_ctx* ctx, double* d_F, double* d_grad, double
  * on a context created on the legacy default stream (it cannot be captured). */
 tnrc_status tnrc_set_graphs(tnrc_ctx* ctx, int32_t enable);
 
+/* F and grad[K][C][N] like tnrc_fidelity_grad, by the plain GPU path: one
+ * trajectory at a time and one launch per step -- a launch per forward layer
+ * whose CTAs (one warp each) take the layer's bonds, one for the overlap,
+ * and per costate layer one for the environments and one for the bonds'
+ * gradients and costate updates -- with every forward layer state kept as a
+ * full slot.  The same device functions as the batched launch, so the
+ * results are bitwise the same; it is the baseline the persistent batched
+ * launch is measured against (no persistent CTAs, no batching across
+ * trajectories, no CUDA graph).  Reserves its own device buffers on first
+ * use ((L+1) full slots for L truncated layers, per-CTA scratch).  Errors as
+ * tnrc_fidelity_grad, and TNRC_E_NOMEM. */
+tnrc_status tnrc_fidelity_grad_plain(tnrc_ctx* ctx, double* F, double* grad);
+
 /* Order the context's later work on another stream (a cudaStream_t; NULL =
  * the legacy default stream, refused while graphs are on).  Waits for the
  * work already queued on the current stream first.  A serving loop uses it

@@ -16,6 +16,9 @@
 
 extern "C" cudaError_t tnrc_launch_traj(const tnrc::TrajParams* p, int grid, size_t smem, cudaStream_t st);
 extern "C" cudaError_t tnrc_traj_prepare();
+extern "C" cudaError_t tnrc_plain_prepare();
+extern "C" cudaError_t tnrc_launch_plain(const tnrc::TrajParams* p, int op, const unsigned char* a,
+                                         unsigned char* b, int s, int l, int t, size_t smem, cudaStream_t st);
 extern "C" cudaError_t tnrc_traj_occupancy(int phys_dim, int min_blocks, int warps, size_t smem, int* per_sm);
 extern "C" cudaError_t tnrc_launch_layer_gates(int N, int K, int C, int M, int terms, int order, int nsub,
                                                int L, int R, int first_parity, double dt, const double* u,
@@ -58,6 +61,8 @@ struct tnrc_ctx {
   bool timed_last = false;        // ev0/ev1 bracket the last evaluation (not a graph replay)
   std::vector<GraphEntry> graphs;
   char err[256] = {0};            // the CUDA failure that made the context unusable
+  // buffers of the plain one-trajectory-at-a-time path (made on first use)
+  unsigned char* plain = nullptr;
   tnrc_stats stats{};
   int n_sm = 0;
   template <class T>
@@ -82,21 +87,10 @@ tnrc_status fail_cuda(tnrc_ctx* c, cudaError_t e, int line) {
     if (ck_e_ != cudaSuccess) return fail_cuda(ctx, ck_e_, __LINE__); \
   } while (0)
 
-tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, double* dper, bool capturing = false) {
+// Trajectory-kernel parameters of a context (the persistent launch's arena
+// regions; other launch forms override what differs).
+tnrc::TrajParams traj_params(tnrc_ctx* ctx, bool grad) {
   Plan& P = ctx->plan;
-  cudaStream_t st = ctx->stream;
-  if (!capturing) CK(cudaEventRecord(ctx->ev0, st));
-  ctx->timed_last = !capturing;
-  if (ctx->gates_dirty) {
-    CK(tnrc_launch_layer_gates(P.N, P.K, P.C, P.M, P.terms, P.order, P.nsub, P.n_layers, P.recs, P.first_parity,
-                               ctx->dt, ctx->at<double>(P.off_u), ctx->at<unsigned char>(P.off_mask),
-                               ctx->at<double>(P.off_gfix), ctx->at<double>(P.off_J), ctx->at<int>(P.off_loff),
-                               ctx->at<tnrc::LayerGate>(P.off_gates), ctx->at<int>(P.off_status), st));
-    ctx->gates_dirty = false;
-  }
-  CK(cudaMemsetAsync(ctx->at<int>(P.off_wc), 0, sizeof(int), st));
-  CK(cudaMemsetAsync(ctx->at<unsigned long long>(P.off_counters), 0, tnrc::kNumCounters * 8, st));
-  CK(cudaMemsetAsync(ctx->at<unsigned long long>(P.off_counters) + tnrc::kCtrGap, 0xff, 8, st));
   tnrc::TrajParams tp{};
   tp.N = P.N;
   tp.K = P.K;
@@ -138,6 +132,25 @@ tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, dou
   tp.counters = ctx->at<unsigned long long>(P.off_counters);
   tp.status = ctx->at<int>(P.off_status);
   tp.work_counter = ctx->at<int>(P.off_wc);
+  return tp;
+}
+
+tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, double* dper, bool capturing = false) {
+  Plan& P = ctx->plan;
+  cudaStream_t st = ctx->stream;
+  if (!capturing) CK(cudaEventRecord(ctx->ev0, st));
+  ctx->timed_last = !capturing;
+  if (ctx->gates_dirty) {
+    CK(tnrc_launch_layer_gates(P.N, P.K, P.C, P.M, P.terms, P.order, P.nsub, P.n_layers, P.recs, P.first_parity,
+                               ctx->dt, ctx->at<double>(P.off_u), ctx->at<unsigned char>(P.off_mask),
+                               ctx->at<double>(P.off_gfix), ctx->at<double>(P.off_J), ctx->at<int>(P.off_loff),
+                               ctx->at<tnrc::LayerGate>(P.off_gates), ctx->at<int>(P.off_status), st));
+    ctx->gates_dirty = false;
+  }
+  CK(cudaMemsetAsync(ctx->at<int>(P.off_wc), 0, sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->at<unsigned long long>(P.off_counters), 0, tnrc::kNumCounters * 8, st));
+  CK(cudaMemsetAsync(ctx->at<unsigned long long>(P.off_counters) + tnrc::kCtrGap, 0xff, 8, st));
+  tnrc::TrajParams tp = traj_params(ctx, grad);
   size_t smem = tnrc_traj_smem(P.warps, P.slab_elems);
   int grid = P.grid;
   if (ctx->pooled) {
@@ -454,6 +467,75 @@ tnrc_status tnrc_set_graphs(tnrc_ctx* ctx, int32_t enable) {
   return TNRC_OK;
 }
 
+tnrc_status tnrc_fidelity_grad_plain(tnrc_ctx* ctx, double* F, double* grad) {
+  if (!ctx || !F || !grad) return TNRC_E_INVALID;
+  if (ctx->broken) return TNRC_E_CUDA;
+  if (!ctx->have_u || !ctx->have_J) return TNRC_E_STATE;
+  Plan& P = ctx->plan;
+  cudaStream_t st = ctx->stream;
+  const int L = P.n_layers;
+  const int64_t sb = P.L.bytes;
+  int nbmax = 0;
+  for (int par = 0; par < 2; ++par) nbmax = std::max(nbmax, (P.N - 1 - par + 1) / 2);
+  const int nscr = std::max(nbmax, 2);
+  // every layer state of the trajectory as a full slot, the costate slot,
+  // per-CTA warp scratch and one environment region
+  const int64_t off_hist = 0, off_c = off_hist + (int64_t)(L + 1) * sb, off_scr = align_up(off_c + sb, 256),
+                off_env = align_up(off_scr + (int64_t)nscr * P.scratch_elems * 16, 256),
+                total = off_env + P.env_elems * 16;
+  if (!ctx->plain && cudaMalloc(&ctx->plain, (size_t)total) != cudaSuccess) {
+    cudaGetLastError();
+    return TNRC_E_NOMEM;
+  }
+  CK(tnrc_plain_prepare());
+  unsigned char* hist = ctx->plain + off_hist;
+  unsigned char* cslot = ctx->plain + off_c;
+  if (ctx->gates_dirty) {
+    CK(tnrc_launch_layer_gates(P.N, P.K, P.C, P.M, P.terms, P.order, P.nsub, P.n_layers, P.recs, P.first_parity,
+                               ctx->dt, ctx->at<double>(P.off_u), ctx->at<unsigned char>(P.off_mask),
+                               ctx->at<double>(P.off_gfix), ctx->at<double>(P.off_J), ctx->at<int>(P.off_loff),
+                               ctx->at<tnrc::LayerGate>(P.off_gates), ctx->at<int>(P.off_status), st));
+    ctx->gates_dirty = false;
+  }
+  CK(cudaMemsetAsync(ctx->at<unsigned long long>(P.off_counters), 0, tnrc::kNumCounters * 8, st));
+  CK(cudaMemsetAsync(ctx->at<unsigned long long>(P.off_counters) + tnrc::kCtrGap, 0xff, 8, st));
+  tnrc::TrajParams tp = traj_params(ctx, true);
+  tp.warps = 2;   // the environment launch runs two warps; the others one
+  tp.slab_elems = std::min(P.d * P.d * P.chi * P.chi, 4096);
+  tp.warp_scratch = reinterpret_cast<double2*>(ctx->plain + off_scr);
+  tp.env_scratch = reinterpret_cast<double2*>(ctx->plain + off_env);
+  const size_t smem = tnrc_traj_smem(2, tp.slab_elems);
+  const unsigned char* in = ctx->at<unsigned char>(P.off_in);
+  const unsigned char* tg = ctx->at<unsigned char>(P.off_tg);
+  const int64_t KCN = (int64_t)P.K * P.C * P.N;
+  CK(cudaEventRecord(ctx->ev0, st));
+  for (int t = 0; t < P.T; ++t) {
+    const int s = t / P.P, pi = t - s * P.P;
+    CK(tnrc_launch_plain(&tp, 0, in + (size_t)pi * sb, hist, 0, 0, 0, 0, st));
+    for (int l = 0; l < L; ++l) {
+      CK(tnrc_launch_plain(&tp, 0, hist + (size_t)l * sb, hist + (size_t)(l + 1) * sb, 0, 0, 0, 0, st));
+      CK(tnrc_launch_plain(&tp, 1, nullptr, hist + (size_t)(l + 1) * sb, s, l, t, smem, st));
+    }
+    CK(tnrc_launch_plain(&tp, 2, tg + (size_t)pi * sb, hist + (size_t)L * sb, 0, 0, t, smem, st));
+    CK(tnrc_launch_plain(&tp, 0, tg + (size_t)pi * sb, cslot, 0, 0, 0, 0, st));
+    CK(cudaMemsetAsync(ctx->at<double>(P.off_gsp) + (size_t)t * KCN, 0, (size_t)KCN * 8, st));
+    for (int l = L - 1; l >= 0; --l) {
+      CK(tnrc_launch_plain(&tp, 3, hist + (size_t)(l + 1) * sb, cslot, s, l, t, smem, st));
+      CK(tnrc_launch_plain(&tp, 4, hist + (size_t)(l + 1) * sb, cslot, s, l, t, smem, st));
+    }
+  }
+  const int X = (int)KCN;
+  CK(tnrc_launch_reduce(ctx->at<double2>(P.off_O), P.T, ctx->at<double>(P.off_F), nullptr,
+                        ctx->at<double>(P.off_gsp), X, ctx->at<double>(P.off_grad), st));
+  CK(cudaEventRecord(ctx->ev1, st));
+  ctx->timed_last = true;
+  tnrc_status r = finish(ctx);
+  if (r != TNRC_OK) return r;
+  CK(cudaMemcpy(F, ctx->at<double>(P.off_F), 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(grad, ctx->at<double>(P.off_grad), (size_t)KCN * 8, cudaMemcpyDeviceToHost));
+  return TNRC_OK;
+}
+
 tnrc_status tnrc_set_stream(tnrc_ctx* ctx, void* cuda_stream) {
   if (!ctx) return TNRC_E_INVALID;
   if (ctx->broken) return TNRC_E_CUDA;
@@ -557,6 +639,7 @@ void tnrc_destroy(tnrc_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->plain) cudaFree(ctx->plain);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   for (auto e : ctx->tev)

@@ -29,7 +29,6 @@ constexpr int kStatusNaN = 2;
 constexpr int kStatusBadDims = 4;
 constexpr int kStatusTimeout = 8;            // a bounded device wait gave up (no free work region)
 constexpr int kRegionTries = 1 << 16;        // region-pool scans before giving up (about a second)
-constexpr long long kEnvWaitCycles = 1ll << 33;   // a warp's wait for environment sweeps (about 4 s)
 constexpr int kCtrPhase = 5 + kMaxChi + 1;      // first of kNumPhases cycle counters
 constexpr int kNumPhases = 9;
 constexpr int kCtrCapTrunc = kCtrPhase + kNumPhases;  // truncations whose cut the cap chi_max decided

@@ -49,8 +49,6 @@ struct WarpCtx {
   int* order;               // shared, CTA-wide: bonds of the current layer by decreasing cost
   int* next;                // shared, CTA-wide: next entry of `order` to take
   int region;               // the CTA's work region (scratch, environments, slots)
-  volatile int* lready;     // shared: left environments L_0 .. L_lready are built
-  volatile int* rready;     // shared: right environments R_rready .. R_N are built
 };
 
 // Algorithmic flops of one two-site update with theta of m x n (m = 2 Dl,
@@ -424,9 +422,7 @@ __device__ void layer_envs(const TrajParams& p, const Lay& Y, const unsigned cha
   double2* Rbuf = Lbuf + (size_t)(N + 1) * cc;
   const int lane = w.lane;
 
-  // left environments L_i (sites < i) for i <= N-2, right R_i (sites >= i)
-  // for i >= 2; each step publishes its progress (after a block-scope fence)
-  // for the warps already working on bonds
+  // left environments L_i (sites < i) for i <= N-2, right R_i (sites >= i) for i >= 2
   TNRC_TIC(t_e);
   if (warp == 0) {
     for (int i = 0; i + 1 <= N - 2; ++i) {
@@ -435,9 +431,6 @@ __device__ void layer_envs(const TrajParams& p, const Lay& Y, const unsigned cha
       env_left_step<kD>(Lbuf + i * cc, Dc[i], Da[i], cs + so[i], Dc[i + 1], as + ao[i], Da[i + 1],
                         tmp, Lbuf + (i + 1) * cc, lane);
       w.alg += 8ull * kD * Da[i + 1] * (unsigned long long)(Dc[i] * Da[i] + Dc[i + 1] * Dc[i]);
-      __syncwarp();
-      __threadfence_block();
-      if (lane == 0) *w.lready = i + 1;
     }
   } else if (warp == 1) {
     for (int i = N - 1; i >= 2; --i) {
@@ -445,36 +438,9 @@ __device__ void layer_envs(const TrajParams& p, const Lay& Y, const unsigned cha
       env_right_step<kD>(Rbuf + (size_t)(i + 1) * cc, Dc[i + 1], Da[i + 1], cs + so[i], Dc[i],
                          as + ao[i], Da[i], tmp, Rbuf + (size_t)i * cc, lane);
       w.alg += 8ull * kD * Da[i] * (unsigned long long)(Dc[i + 1] * Da[i + 1] + Dc[i] * Dc[i + 1]);
-      __syncwarp();
-      __threadfence_block();
-      if (lane == 0) *w.rready = i;
     }
   }
   TNRC_TOC(w, 4, t_e);
-}
-
-// Waits (bounded) until both environment sweeps are past sites b and b+1:
-// bond b's gradient then has L_b and R_{b+2}, and its costate update may
-// rewrite the two sites, which neither sweep reads again.  Gives up after
-// kEnvWaitCycles SM cycles (a few seconds, far beyond any sweep) with the
-// timeout status set.
-__device__ inline void wait_envs(const TrajParams& p, int b, WarpCtx& w) {
-  const int lneed = min(b + 2, p.N - 2), rneed = max(b, 2);
-  int ok = 1;
-  if (w.lane == 0) {
-    const long long t0 = clock64();
-    while (*w.lready < lneed || *w.rready > rneed) {
-      if (clock64() - t0 > kEnvWaitCycles) {
-        ok = 0;
-        break;
-      }
-      __nanosleep(128);
-    }
-  }
-  __syncwarp();
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  if (!ok && w.lane == 0) atomicOr(p.status, kStatusTimeout);
-  __threadfence_block();
 }
 
 template <int kD>
@@ -650,16 +616,15 @@ __device__ void apply_layer(const TrajParams& p, const Lay& Y, unsigned char* sl
   TNRC_TOC(w, 7, t_b);
 }
 
-// One layer of the costate sweep (App. A): the environments of <c_l|.|a_l>,
-// and every bond of layer l -- largest first from the shared counter -- its
-// gradient and at once its costate update c_{l-1} = G^dag c_l, which reuses
-// the product c_b c_{b+1} the gradient formed.  Warps 0 and 1 build the left
-// and right environments; the other warps start on a bond as soon as both
-// sweeps are past its two sites (the middle bonds, the largest, come free
-// first), and warps 0 and 1 join when their sweeps end.  A bond's gradient
-// reads only its own two costate sites and the environments; its update
-// rewrites those two sites, which no other bond of the layer and neither
-// sweep touches afterwards.
+// One layer of the costate sweep (App. A): the environments of <c_l|.|a_l>
+// (warps 0 and 1), then every bond of layer l -- largest first from the
+// shared counter -- its gradient and at once its costate update
+// c_{l-1} = G^dag c_l, which reuses the product c_b c_{b+1} the gradient
+// formed.  A bond's gradient reads only its own two costate sites and the
+// environments; its update rewrites those two sites, which no other bond of
+// the layer touches.  (Starting bonds while the environment sweeps still run
+// -- as soon as both are past the bond's sites -- measured slower: the sweeps
+// then share the FP64 pipes and the edge bonds wait for them all the same.)
 template <int kD>
 __device__ void costate_layer(const TrajParams& p, const Lay& Y, unsigned char* cslot, const StateView av, int s,
                               int l, double2 wO, double* gsp_row, WarpCtx& w, int warp) {
@@ -674,18 +639,16 @@ __device__ void costate_layer(const TrajParams& p, const Lay& Y, unsigned char* 
     double2* Lbuf = p.env_scratch + (size_t)w.region * 2 * (p.N + 1) * cc;
     Lbuf[0] = make_double2(1.0, 0.0);
     Lbuf[(size_t)(2 * p.N + 1) * cc] = make_double2(1.0, 0.0);   // R_N
-    *w.lready = 0;
-    *w.rready = p.N;
   }
   __syncthreads();
   layer_envs<kD>(p, Y, cslot, av, w, warp);
+  __syncthreads();
   for (;;) {
     int j = 0;
     if (lane == 0) j = atomicAdd(w.next, 1);
     j = __shfl_sync(0xffffffffu, j, 0);
     if (j >= nb) break;
     const int b = w.order[j];
-    wait_envs(p, b, w);
     double2* th = theta_home(p, kDD, kDD * Dc[b] * Dc[b + 2], w);
     bond_gradient<kD>(p, Y, cslot, av, s, l, b, wO, gsp_row, w, th);
     two_site_update<kD>(p, Y, cslot, b, layer_rec(p, s, l, b).G, true, false, true, w, th);
@@ -804,7 +767,6 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) traj_kernel(TrajParam
   __shared__ int s_order[128];
   __shared__ int s_next;
   __shared__ int s_region;
-  __shared__ int s_lready, s_rready;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   double2* slabs = reinterpret_cast<double2*>(smem_raw);
@@ -857,8 +819,6 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) traj_kernel(TrajParam
   for (int i = 0; i < kNumPhases; ++i) w.ph[i] = 0;
   w.order = s_order;
   w.next = &s_next;
-  w.lready = &s_lready;
-  w.rready = &s_rready;
   unsigned char* base = p.work + (size_t)region * p.work_stride;
 
   for (int iter = 0;; ++iter) {
@@ -901,7 +861,159 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) traj_kernel(TrajParam
   }
 }
 
+// ---------------------------------------------------------------------------
+// The plain GPU path: one trajectory at a time, one launch per step, the
+// bonds of a layer spread over CTAs of one warp each (the whole GPU for one
+// trajectory, as far as its layers have bonds).  It runs the same device
+// functions as the batched kernel and gives bitwise the same results; it is
+// the baseline that the persistent batched launch is measured against.
+// ---------------------------------------------------------------------------
+struct PlainShared {
+  double2* slab;
+  double* sig;
+  double* qn;
+  int* perm;
+  int* piv;
+  double2* small;
+};
+
+__device__ inline void plain_warp(const TrajParams& p, WarpCtx& w, int scratch_index, int* order, int* next,
+                                  int warp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* slabs = reinterpret_cast<double2*>(smem_raw);
+  double* sig = reinterpret_cast<double*>(slabs + (size_t)p.warps * p.slab_elems);
+  double* qns = sig + (size_t)p.warps * kMaxDim;
+  int* perms = reinterpret_cast<int*>(qns + (size_t)p.warps * kMaxDim);
+  int* pivs = perms + (size_t)p.warps * kMaxDim;
+  double2* smalls = reinterpret_cast<double2*>(pivs + (size_t)p.warps * kMaxDim);
+  w.region = 0;   // the one environment region
+  w.slab = slabs + (size_t)warp * p.slab_elems;
+  w.scratch = p.warp_scratch + (size_t)scratch_index * p.scratch_elems;
+  w.sig2 = sig + (size_t)warp * kMaxDim;
+  w.perm = perms + (size_t)warp * kMaxDim;
+  w.qn = qns + (size_t)warp * kMaxDim;
+  w.piv = pivs + (size_t)warp * kMaxDim;
+  w.small = smalls + (size_t)warp * 64;
+  w.lane = threadIdx.x & 31;
+  w.sweeps = w.updates = w.capcuts = 0;
+  w.alg = 0;
+  w.disc = 0.0;
+  w.maxk = 0;
+  for (int i = 0; i < kNumPhases; ++i) w.ph[i] = 0;
+  w.order = order;
+  w.next = next;
+}
+
+// Copy a full slot (one CTA).
+template <int kD>
+__global__ void plain_copy_kernel(TrajParams p, const unsigned char* src, unsigned char* dst) {
+  copy_slot<kD>(p, p.full, src, p.full, dst);
+}
+
+// Forward layer l of trajectory (s, .) on `slot`: CTA j updates the j-th bond.
+template <int kD>
+__global__ void __launch_bounds__(32) plain_fwd_kernel(TrajParams p, unsigned char* slot, int s, int l) {
+  __shared__ int s_order[1], s_next;
+  WarpCtx w;
+  plain_warp(p, w, blockIdx.x, s_order, &s_next, 0);
+  const int b = layer_parity(p, l) + 2 * (int)blockIdx.x;
+  two_site_update<kD>(p, p.full, slot, b, layer_rec(p, s, l, b).G, false, true, true, w);
+  if (w.lane == 0) atomicAdd(&p.counters[1], (unsigned long long)w.sweeps);
+}
+
+// O_t = <t_p | a_t> (one warp).
+template <int kD>
+__global__ void __launch_bounds__(32) plain_overlap_kernel(TrajParams p, const unsigned char* tg,
+                                                           const unsigned char* a, int t) {
+  __shared__ int s_order[1], s_next;
+  WarpCtx w;
+  plain_warp(p, w, 0, s_order, &s_next, 0);
+  const double2 O = warp_overlap<kD>(p, p.full, tg, p.full, a, w);
+  if (w.lane == 0) p.O[t] = O;
+}
+
+// Environments of <c|.|a_l> for layer l (two warps: left and right sweeps).
+template <int kD>
+__global__ void __launch_bounds__(64) plain_envs_kernel(TrajParams p, const unsigned char* cslot,
+                                                        const unsigned char* aslot) {
+  __shared__ int s_order[1], s_next;
+  WarpCtx w;
+  const int warp = threadIdx.x >> 5;
+  plain_warp(p, w, warp, s_order, &s_next, warp);
+  const size_t cc = (size_t)p.chi * p.chi;
+  if (threadIdx.x == 0) {
+    p.env_scratch[0] = make_double2(1.0, 0.0);
+    p.env_scratch[(size_t)(2 * p.N + 1) * cc] = make_double2(1.0, 0.0);
+  }
+  __syncthreads();
+  layer_envs<kD>(p, p.full, cslot, slot_view(aslot, p.full), w, warp);
+}
+
+// Gradient and costate update of the bonds of layer l (CTA j: the j-th bond).
+template <int kD>
+__global__ void __launch_bounds__(32) plain_bwd_kernel(TrajParams p, unsigned char* cslot, const unsigned char* aslot,
+                                                       int s, int l, int t) {
+  __shared__ int s_order[1], s_next;
+  WarpCtx w;
+  plain_warp(p, w, blockIdx.x, s_order, &s_next, 0);
+  const int b = layer_parity(p, l) + 2 * (int)blockIdx.x;
+  const int* Dc = slot_dims(cslot);
+  double2* th = theta_home(p, kD * kD, kD * kD * Dc[b] * Dc[b + 2], w);
+  bond_gradient<kD>(p, p.full, cslot, slot_view(aslot, p.full), s, l, b, p.O[t],
+                    p.gsp + (size_t)t * p.K * p.C * p.N, w, th);
+  two_site_update<kD>(p, p.full, cslot, b, layer_rec(p, s, l, b).G, true, false, true, w, th);
+  if (w.lane == 0) atomicAdd(&p.counters[1], (unsigned long long)w.sweeps);
+}
+
 }  // namespace tnrc
+
+// Host launchers of the plain path (see above).  `op`: 0 copy, 1 forward
+// layer, 2 overlap, 3 environments, 4 gradient and costate update.
+extern "C" cudaError_t tnrc_launch_plain(const tnrc::TrajParams* p, int op, const unsigned char* a,
+                                         unsigned char* b, int s, int l, int t, size_t smem, cudaStream_t st) {
+  (void)cudaGetLastError();
+  const int nb = (p->N - 1 - ((l + p->first_parity) & 1) + 1) / 2;
+  const bool d4 = p->phys_dim == 4;
+  switch (op) {
+    case 0:
+      if (d4) tnrc::plain_copy_kernel<4><<<1, 256, 0, st>>>(*p, a, b);
+      else tnrc::plain_copy_kernel<2><<<1, 256, 0, st>>>(*p, a, b);
+      break;
+    case 1:
+      if (d4) tnrc::plain_fwd_kernel<4><<<nb, 32, smem, st>>>(*p, b, s, l);
+      else tnrc::plain_fwd_kernel<2><<<nb, 32, smem, st>>>(*p, b, s, l);
+      break;
+    case 2:
+      if (d4) tnrc::plain_overlap_kernel<4><<<1, 32, smem, st>>>(*p, a, b, t);
+      else tnrc::plain_overlap_kernel<2><<<1, 32, smem, st>>>(*p, a, b, t);
+      break;
+    case 3:
+      if (d4) tnrc::plain_envs_kernel<4><<<1, 64, smem, st>>>(*p, b, a);
+      else tnrc::plain_envs_kernel<2><<<1, 64, smem, st>>>(*p, b, a);
+      break;
+    case 4:
+      if (d4) tnrc::plain_bwd_kernel<4><<<nb, 32, smem, st>>>(*p, b, a, s, l, t);
+      else tnrc::plain_bwd_kernel<2><<<nb, 32, smem, st>>>(*p, b, a, s, l, t);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+extern "C" cudaError_t tnrc_plain_prepare() {
+  cudaError_t e = cudaSuccess;
+  const int lim = 200 * 1024;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(tnrc::plain_fwd_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(tnrc::plain_fwd_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(tnrc::plain_overlap_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(tnrc::plain_overlap_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(tnrc::plain_envs_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(tnrc::plain_envs_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(tnrc::plain_bwd_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(tnrc::plain_bwd_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  return e;
+}
 
 // host-side launcher; tnrc_create (and the allocation-free entry point) raise
 // the shared-memory limit with tnrc_traj_prepare before any launch or capture

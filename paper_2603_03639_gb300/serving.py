@@ -17,8 +17,8 @@ own noise seed.  The server
     as soon as any running trajectory ends (continuous batching at trajectory
     granularity); requests of problems that have been quick run on a
     high-priority stream, so the block scheduler starts their CTAs before the
-    pending CTAs of long requests, and when admission is full the pending
-    request with the shortest measured work is admitted first;
+    pending CTAs of long requests; pending requests are admitted shortest
+    measured work first, and a short request even past the in-flight cap;
   * completes a request when its stream's event has fired, copying F and the
     gradient back, and records arrival, start and finish times.
 
@@ -150,7 +150,8 @@ class Server:
     """Continuous-batching server on one device.
 
     mem_budget: device bytes the resident contexts may hold (default: 60% of
-    the free memory at start); max_inflight: requests on the device at once;
+    the free memory at start); max_inflight: requests on the device at once
+    (short requests may exceed it, up to four times);
     short_s: a request whose problem has been served in at most this many
     seconds of device time runs on a high-priority stream, so that its CTAs
     start before the pending CTAs of longer requests (shortest work first at
@@ -295,8 +296,14 @@ class Server:
                 # (arrival order among equals): a short request does not wait
                 # behind long ones for admission either
                 inflight = sum(1 for s in self.slots if s.busy is not None)
-                while self.pending and inflight < self.max_inflight:
+                while self.pending:
                     req = self._next_pending()
+                    t = self._service(req.key)
+                    short = t is not None and t <= self.short_s
+                    # a short request is admitted past the in-flight cap (up to
+                    # four times it): its CTAs take SM slots as trajectories end
+                    if inflight >= (4 * self.max_inflight if short else self.max_inflight):
+                        break
                     try:
                         admitted = self._admit(req)
                     except Exception as e:  # creation or launch failed: fail this request only

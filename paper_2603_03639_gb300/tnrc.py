@@ -22,7 +22,7 @@ EXPORTS = ("tnrc_create", "tnrc_set_controls", "tnrc_sample_noise", "tnrc_set_no
            "tnrc_fidelity_grad", "tnrc_get_overlaps", "tnrc_get_stats", "tnrc_set_controls_dev",
            "tnrc_evaluate_dev", "tnrc_sync", "tnrc_footprint", "tnrc_destroy", "tnrc_status_string",
            "tnrc_fidelity_static", "tnrc_set_graphs", "tnrc_last_error", "tnrc_measure_fp64_peak",
-           "tnrc_measure_dmma_peak", "tnrc_set_pooled", "tnrc_set_stream")
+           "tnrc_measure_dmma_peak", "tnrc_set_pooled", "tnrc_set_stream", "tnrc_fidelity_grad_plain")
 
 
 class TNRCError(RuntimeError):
@@ -97,6 +97,8 @@ def lib() -> ctypes.CDLL:
         L.tnrc_set_pooled.restype = i32
         L.tnrc_set_stream.argtypes = [vp, vp]
         L.tnrc_set_stream.restype = i32
+        L.tnrc_fidelity_grad_plain.argtypes = [vp, dp, dp]
+        L.tnrc_fidelity_grad_plain.restype = i32
         L.tnrc_footprint.argtypes = [ctypes.POINTER(Problem)]
         L.tnrc_footprint.restype = ctypes.c_size_t
         L.tnrc_destroy.argtypes = [vp]
@@ -297,6 +299,13 @@ class Context:
         F = np.zeros(1)
         g = np.zeros((self.K, self.C, self.N))
         _check(lib().tnrc_fidelity_grad(self._h, _dp(F), _dp(g)), "tnrc_fidelity_grad", self._h)
+        return F[0], g
+
+    def fidelity_grad_plain(self):
+        """F and dF/du by the plain one-trajectory-at-a-time GPU path."""
+        F = np.zeros(1)
+        g = np.zeros((self.K, self.C, self.N))
+        _check(lib().tnrc_fidelity_grad_plain(self._h, _dp(F), _dp(g)), "tnrc_fidelity_grad_plain", self._h)
         return F[0], g
 
     def overlaps(self) -> np.ndarray:

@@ -374,3 +374,24 @@ def test_pooled_launch_equals_persistent_launch():
         ctx.sync()
         assert F.item() == out[False][0] and np.array_equal(g.cpu().numpy(), out[False][1])
     ctx.close()
+
+
+@pytest.mark.parametrize("name", ["truncated", "operator"])
+def test_plain_path_equals_batched_launch(name):
+    """tnrc_fidelity_grad_plain (one trajectory at a time, one launch per
+    step) runs the batched kernel's device functions: bitwise the same F and
+    gradient, and the oracle's within the bars."""
+    if name == "truncated":
+        w = synth.WORKLOADS["ghz30"].replace(N=12, K=4, chi=32, M=2, P=1, u_sigma=1.5, dt=0.25)
+    else:
+        w = synth.WORKLOADS["cnotgate50"].replace(N=6, K=3, chi=8, M=2)
+    u, mask, J, ins, tgs = case(w)
+    ctx = gpu_context(w, ins, tgs, mask)
+    ctx.set_controls(u)
+    ctx.set_noise(J)
+    F, g = ctx.fidelity_grad()
+    Fp, gp = ctx.fidelity_grad_plain()
+    assert Fp == F and np.array_equal(gp, g)
+    Fo, go, _ = robust.ensemble(oracle_problem(w, u, mask, J, ins, tgs))
+    assert abs(Fp - Fo) <= TOL_F
+    assert grad_close(gp, go)
