@@ -195,12 +195,14 @@ def reference_arm(args, w):
 KERNEL_SOURCES = ("svd_warp.cuh", "tnrc_device.cuh", "traj.cu")
 
 
-def recorded_traffic(workload):
-    """DRAM bytes per trajectory-kernel launch from the committed ncu summary
-    for this workload, or None when there is none or the kernel sources have
-    changed since it was taken (the summary records their SHA-256)."""
+def recorded_counters(workload):
+    """ncu counters of the trajectory kernel recorded for this workload in
+    profiles/traj_kernel_<workload>_counters.txt -- DRAM bytes per slice-step
+    and executed FP64 flops per algorithmic flop, both from one capture of a
+    cut of the workload -- or None when there is no record or the kernel
+    sources have changed since it was taken (the record holds their SHA-256)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "traj_kernel_%s_traffic.txt" % workload)
+    path = os.path.join(ROOT, "profiles", "traj_kernel_%s_counters.txt" % workload)
     if not os.path.exists(path):
         return None
     rec = {}
@@ -215,7 +217,9 @@ def recorded_traffic(workload):
     if rec.get("workload") != workload or rec.get("kernel_sources_sha256") != h.hexdigest():
         return None
     try:
-        return int(rec["bytes_per_launch"])
+        return {"bytes_per_slice_step": float(rec["dram_bytes_per_slice_step"]),
+                "executed_per_alg": float(rec["executed_fp64_flops_per_alg_flop"]),
+                "fp64_pipe_pct": float(rec["fp64_pipe_active_pct"])}
     except (KeyError, ValueError):
         return None
 
@@ -329,7 +333,11 @@ def gpu_arm(args, w):
     from paper_2603_03639_gb300.tnrc import measure_dmma_peak
     measured_dmma = measure_dmma_peak(probe.data_ptr(), probe.numel() * 8) / 1e3
     achieved = (alg / launches) / (traj_ms / launches / 1000.0) / 1e12 if launches else None
-    traffic = recorded_traffic(w.name)
+    rec = recorded_counters(w.name)
+    traffic = int(rec["bytes_per_slice_step"] * w.slice_steps) if rec else None
+    # executed FP64 work: the recorded ratio of executed (2 DFMA + DADD + DMUL,
+    # thread level) to algorithmic flops applied to this launch's algorithmic rate
+    exec_tf = achieved * rec["executed_per_alg"] if (rec and achieved) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -345,9 +353,16 @@ def gpu_arm(args, w):
                          "source": "autotune cache" if tuned[0] else "default"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "traffic_source": ("ncu dram bytes of a 152-trajectory launch scaled to this launch's "
-                                        "trajectories (profiles/traj_kernel_%s_traffic.txt)" % w.name)
-                     if traffic else "no ncu record for these kernel sources",
+                     "frac_executed": (exec_tf / peak) if exec_tf else None,
+                     "frac_note": ("frac divides the nominal algorithmic count (the thin-SVD formula on the "
+                                   "full theta, contractions, environments) by the kernel time; frac_executed "
+                                   "divides the FP64 work the kernel executed (ncu)"
+                                   + ("; a nominal frac above about 1.2 reflects the count, not the pipe"
+                                      if achieved and achieved / peak > 1.2 else "")),
+                     "executed_tflops": exec_tf,
+                     "counters_source": ("ncu counters of a cut of this workload, per slice-step "
+                                         "(profiles/traj_kernel_%s_counters.txt)" % w.name)
+                     if rec else "no ncu record for these kernel sources",
                      "kernel": "tnrc::traj_kernel",
                      "peak_source": "derived FP64 FMA peak: 2 DFMA/clk/SM x 152 SMs x 2070 MHz",
                      "measured_fp64_fma_peak": measured_peak,
@@ -451,13 +466,16 @@ def served_run(probs, arrivals, reqs, max_inflight=8):
     """The continuous-batching server (pooled launches, priority streams)."""
     from paper_2603_03639_gb300.serving import Request, Server
     srv = Server(max_inflight=max_inflight)
-    # make every problem resident first (context creation is not request
-    # latency); two warm requests each, so the server knows their sizes
+    # make every problem resident first, two copies each (context creation is
+    # not request latency, and two requests of one problem can then be in
+    # flight at once), and let the server measure their sizes
     for key, w, ins, tgs in probs:
         for _ in range(2):
-            srv.submit(Request(key=key, N=w.N, K=w.K, dt=w.dt, chi=w.chi, M=w.M, C=w.C, inputs=ins, targets=tgs,
-                               controls=np.zeros((w.K, w.C, w.N)), noise_seed=1, noise_dist=w.noise_dist,
-                               noise_scale=w.noise_scale, want_grad=True, mask=w.mask()))
+            for _ in range(2):
+                srv.submit(Request(key=key, N=w.N, K=w.K, dt=w.dt, chi=w.chi, M=w.M, C=w.C, inputs=ins,
+                                   targets=tgs, controls=np.zeros((w.K, w.C, w.N)), noise_seed=1,
+                                   noise_dist=w.noise_dist, noise_scale=w.noise_scale, want_grad=True,
+                                   mask=w.mask()))
             srv.drain()
     t0 = time.perf_counter()
     for r, t in zip(reqs, arrivals):
@@ -467,8 +485,10 @@ def served_run(probs, arrivals, reqs, max_inflight=8):
         srv.submit(r)
     srv.drain()
     peak = srv.peak_inflight
+    made = len(srv.slots)
     srv.close()
-    return {"peak_inflight": peak, "high_priority": sum(1 for r in reqs if r.priority == "high")}
+    return {"peak_inflight": peak, "high_priority": sum(1 for r in reqs if r.priority == "high"),
+            "resident_contexts": made}
 
 
 def plain_run(probs, arrivals, reqs):

@@ -501,7 +501,7 @@ tnrc_status tnrc_fidelity_grad_plain(tnrc_ctx* ctx, double* F, double* grad) {
   CK(cudaMemsetAsync(ctx->at<unsigned long long>(P.off_counters) + tnrc::kCtrGap, 0xff, 8, st));
   tnrc::TrajParams tp = traj_params(ctx, true);
   tp.warps = 2;   // the environment launch runs two warps; the others one
-  tp.slab_elems = std::min(P.d * P.d * P.chi * P.chi, 4096);
+  tp.slab_elems = P.slab_elems;   // the batched launch's slab: the same bonds go as pairs
   tp.warp_scratch = reinterpret_cast<double2*>(ctx->plain + off_scr);
   tp.env_scratch = reinterpret_cast<double2*>(ctx->plain + off_env);
   const size_t smem = tnrc_traj_smem(2, tp.slab_elems);

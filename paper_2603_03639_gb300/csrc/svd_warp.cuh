@@ -322,6 +322,267 @@ __device__ inline int warp_qrcp(double2* W, int m, int n, double thr, int* piv, 
   return steps;
 }
 
+// ---------------------------------------------------------------------------
+// Two matrices per warp.  For small matrices a Jacobi round costs mostly its
+// per-pair scalars (inner products reduced, two reciprocal square roots, the
+// norm updates), which every lane of a pair's group computes: with few pairs
+// per round most of a round's FP64 instructions are that fixed part.  Two
+// matrices on the two half-warps share those instructions -- the halves run
+// the same instruction stream on different data -- at the price of twice
+// the rows per lane.  Lane hb + ll (hb = 0 or 16, ll < 16) works on the
+// matrix of its half; every loop containing a warp-wide barrier runs to the
+// larger of the two trip counts, the half that is done idling.
+// ---------------------------------------------------------------------------
+
+__device__ inline void half_col_norms(const double2* T, int n, int m, double* out, int ll, int hb) {
+  const int g = (m >= 16 || m < 1) ? 1 : 16 / m;
+  const int gi = ll / g, lig = ll - gi * g, gb = hb + gi * g;
+  const int groups = 16 / g;
+  const unsigned gmask = group_mask(g, gb);
+  for (int c = gi; c < m && gi < groups; c += groups) {
+    const double2* col = T + (size_t)c * n;
+    double s = 0.0;
+    for (int row = lig; row < n; row += g) s = fma(col[row].x, col[row].x, fma(col[row].y, col[row].y, s));
+    if (g > 1) s = group_sum(s, g, lig, gb, gmask);
+    if (lig == 0) out[c] = s;
+  }
+}
+
+// warp_qrcp on each half's matrix (W m x n row-major, thr, piv, qn its own);
+// returns this half's numerical rank.
+__device__ inline int half_qrcp(double2* W, int m, int n, double thr, int* piv, double* qn, int lane) {
+  const int hb = lane & 16, ll = lane & 15;
+  const unsigned hmask = 0xffffu << hb;
+  {
+    const int G = n >= 16 ? 1 : 16 / n;
+    const int groups = 16 / G;
+    const int gi = ll / G, lig = ll - gi * G, gb = hb + gi * G;
+    const unsigned gmask = group_mask(G, gb);
+    for (int c = gi; c < n && gi < groups; c += groups) {
+      double q = 0.0;
+      for (int i = lig; i < m; i += G) q += cabs2(W[(size_t)i * n + c]);
+      if (G > 1) q = group_sum(q, G, lig, gb, gmask);
+      if (lig == 0) {
+        qn[c] = q;
+        piv[c] = c;
+      }
+    }
+  }
+  __syncwarp();
+  const int steps_own = m < n ? m : n;
+  const int steps = __reduce_max_sync(0xffffffffu, (unsigned)steps_own);
+  int rank = steps_own;
+  bool done = false;
+  for (int j = 0; j < steps; ++j) {
+    done = done || (j >= steps_own);
+    // pivot: the column c >= j of largest remaining norm (within the half)
+    long long best = -1;
+    int bi = n;
+    if (!done) {
+      for (int c = j + ll; c < n; c += 16) {
+        const long long v = __double_as_longlong(qn[c]);
+        if (v > best) {
+          best = v;
+          bi = c;
+        }
+      }
+    }
+    for (int o = 8; o > 0; o >>= 1) {
+      const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    const double xn2 = __longlong_as_double(best);
+    if (!done && !(xn2 > thr)) {
+      rank = j;
+      done = true;
+    }
+    if (!done && bi != j) {
+      for (int i = ll; i < m; i += 16) {
+        const double2 t = W[(size_t)i * n + j];
+        W[(size_t)i * n + j] = W[(size_t)i * n + bi];
+        W[(size_t)i * n + bi] = t;
+      }
+      if (ll == 0) {
+        const int tp = piv[j];
+        piv[j] = piv[bi];
+        piv[bi] = tp;
+        qn[bi] = qn[j];
+        qn[j] = xn2;
+      }
+    }
+    __syncwarp();
+    double xn = 0.0;
+    double2 ph = make_double2(1.0, 0.0);
+    if (!done) {
+      const double2 x0 = W[(size_t)j * n + j];
+      xn = sqrt(xn2);
+      const double ax0 = sqrt(cabs2(x0));
+      ph = (ax0 > 0.0) ? cscale(x0, 1.0 / ax0) : make_double2(1.0, 0.0);
+      const double2 v0 = cscale(ph, ax0 + xn);
+      const double beta = 1.0 / (xn * (xn + ax0));
+      const int na = n - j - 1;
+      if (na > 0) {
+        const int G = na >= 16 ? 1 : 16 / na;
+        const int groups = 16 / G;
+        const int gi = ll / G, lig = ll - gi * G, gb = hb + gi * G;
+        const unsigned gmask = group_mask(G, gb);
+        for (int c = j + 1 + gi; c < n && gi < groups; c += groups) {
+          double2 sacc = make_double2(0.0, 0.0);
+          for (int i = j + lig; i < m; i += G) {
+            const double2 vi = (i == j) ? v0 : W[(size_t)i * n + j];
+            cfmac(sacc, vi, W[(size_t)i * n + c]);
+          }
+          if (G > 1) {
+            sacc.x = group_sum(sacc.x, G, lig, gb, gmask);
+            sacc.y = group_sum(sacc.y, G, lig, gb, gmask);
+          }
+          sacc = cscale(sacc, beta);
+          double q = 0.0;
+          for (int i = j + lig; i < m; i += G) {
+            const double2 vi = (i == j) ? v0 : W[(size_t)i * n + j];
+            double2 x = W[(size_t)i * n + c];
+            x.x = fma(-vi.x, sacc.x, x.x);
+            x.x = fma(vi.y, sacc.y, x.x);
+            x.y = fma(-vi.x, sacc.y, x.y);
+            x.y = fma(-vi.y, sacc.x, x.y);
+            W[(size_t)i * n + c] = x;
+            if (i > j) q += cabs2(x);
+          }
+          if (G > 1) q = group_sum(q, G, lig, gb, gmask);
+          if (lig == 0) qn[c] = q;
+        }
+      }
+    }
+    __syncwarp();
+    if (!done)
+      for (int i = j + ll; i < m; i += 16)
+        W[(size_t)i * n + j] = (i == j) ? make_double2(-xn * ph.x, -xn * ph.y) : make_double2(0.0, 0.0);
+    __syncwarp();
+  }
+  (void)hmask;
+  return rank;
+}
+
+// warp_jacobi on each half's matrix (T n x m column-major, fro2, cn its own);
+// returns this half's sweep count (or -kMaxSweeps).
+__device__ inline int half_jacobi(double2* T, int n, int m, double fro2, double* cn, int lane) {
+  const int hb = lane & 16, ll = lane & 15;
+  const unsigned hmask = 0xffffu << hb;
+  const int mp = m + (m & 1);
+  const int P = mp >> 1;
+  const int q0 = m & 1;
+  const int Pe = P - q0;
+  const bool trivial = (mp < 2 || n < 1 || Pe < 1);
+  const int g = (trivial || Pe >= 16) ? 1 : 16 / Pe;
+  const int groups = 16 / g;
+  const int gi = ll / g, lig = ll - gi * g, gb = hb + gi * g;
+  const unsigned gmask = group_mask(g, gb);
+  const double thr = kJacobiZero * kJacobiZero * fro2;
+  const double tol = 2.0 * (double)(m > n ? m : n) * 2.220446049250313e-16;
+  const double tol2 = tol * tol;
+  if (!trivial) half_col_norms(T, n, m, cn, ll, hb);
+  __syncwarp();
+  const int rounds = __reduce_max_sync(0xffffffffu, (unsigned)(trivial ? 0 : mp - 1));
+  bool active = !trivial;
+  int result = trivial ? ((mp < 2 || n < 1) ? 0 : 1) : -kMaxSweeps;
+  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    if (!__any_sync(0xffffffffu, active)) break;
+    int rotated = 0, large = 0;
+    for (int r = 0; r < rounds; ++r) {
+      if (active && r < mp - 1) {
+        for (int q = q0 + gi; q < P && gi < groups; q += groups) {
+          int i, j;
+          rr_pair(mp, r, q, i, j);
+          double2* a = T + (size_t)i * n;
+          double2* b = T + (size_t)j * n;
+          double aa, bb;
+          double2 ab = make_double2(0.0, 0.0);
+          if (r == 0) {
+            aa = 0.0;
+            bb = 0.0;
+            for (int row = lig; row < n; row += g) {
+              const double2 x = a[row], y = b[row];
+              aa = fma(x.x, x.x, fma(x.y, x.y, aa));
+              bb = fma(y.x, y.x, fma(y.y, y.y, bb));
+              cfmac(ab, x, y);
+            }
+            if (g > 1) {
+              aa = group_sum(aa, g, lig, gb, gmask);
+              bb = group_sum(bb, g, lig, gb, gmask);
+              ab.x = group_sum(ab.x, g, lig, gb, gmask);
+              ab.y = group_sum(ab.y, g, lig, gb, gmask);
+            }
+          } else {
+            aa = cn[i];
+            bb = cn[j];
+            for (int row = lig; row < n; row += g) cfmac(ab, a[row], b[row]);
+            if (g > 1) {
+              ab.x = group_sum(ab.x, g, lig, gb, gmask);
+              ab.y = group_sum(ab.y, g, lig, gb, gmask);
+            }
+          }
+          double na = aa, nb = bb;
+          const double ab2 = cabs2(ab);
+          const double pab = aa * bb;
+          if (aa > thr && bb > thr && ab2 > tol2 * pab) {
+            rotated = 1;
+            large |= (ab2 > kJacobiQuad * pab) ? 1 : 0;
+            const double d = bb - aa;
+            const double w = rsqrt(fma(d, d, 4.0 * ab2));
+            const double hq = fma(0.5, fabs(d) * w, 0.5);   // c^2
+            const double rc = rsqrt(hq);
+            const double c = hq * rc;
+            const double f = copysign(w * rc, d);
+            const double2 sp = make_double2(f * ab.x, f * ab.y);
+            for (int row = lig; row < n; row += g) {
+              const double2 x = a[row], y = b[row];
+              double2 na_ = cscale(x, c);
+              na_.x = fma(-sp.x, y.x, na_.x);
+              na_.x = fma(-sp.y, y.y, na_.x);
+              na_.y = fma(-sp.x, y.y, na_.y);
+              na_.y = fma(sp.y, y.x, na_.y);
+              double2 nb_ = cscale(y, c);
+              cfma(nb_, sp, x);
+              a[row] = na_;
+              b[row] = nb_;
+            }
+            const double dl = copysign(2.0 * ab2 * w, d);
+            na = fma(hq, aa, fma(1.0 - hq, bb, -dl));
+            nb = fma(hq, bb, fma(1.0 - hq, aa, dl));
+            if (na < 0.0625 * aa) {
+              na = 0.0;
+              for (int row = lig; row < n; row += g) na = fma(a[row].x, a[row].x, fma(a[row].y, a[row].y, na));
+              if (g > 1) na = group_sum(na, g, lig, gb, gmask);
+            }
+            if (nb < 0.0625 * bb) {
+              nb = 0.0;
+              for (int row = lig; row < n; row += g) nb = fma(b[row].x, b[row].x, fma(b[row].y, b[row].y, nb));
+              if (g > 1) nb = group_sum(nb, g, lig, gb, gmask);
+            }
+          }
+          if (lig == 0) {
+            cn[i] = na;
+            cn[j] = nb;
+          }
+        }
+      }
+      __syncwarp();
+    }
+    // per half: converged after a sweep without rotations, or with only tiny ones
+    const unsigned rot = __ballot_sync(0xffffffffu, rotated) & hmask;
+    const unsigned big = __ballot_sync(0xffffffffu, large) & hmask;
+    if (active && (rot == 0u || big == 0u)) {
+      active = false;
+      result = sweep + 1;
+    }
+  }
+  return result;
+}
+
 // Column norms, ranking and the truncation decision after warp_jacobi.
 // sig2[j] = |column j|^2 (j < m); perm[i] = column of rank i (i <= k, i < m),
 // ranks by decreasing sigma with ties broken by the smaller index.  Returns

@@ -87,23 +87,33 @@ __device__ __forceinline__ double2* theta_home(const TrajParams& p, int kDD, int
 // numerical rank), then one-sided Jacobi on the r columns of R^dagger:
 // R^dagger V = Z S, so theta = (Q V) S (P Z)^dagger and Y = P Z.
 // ---------------------------------------------------------------------------
+// Per-matrix work arrays of the SVD (shared, per warp): squared singular
+// values, column norms (later 1 / sigma), rank order, QR column pivots.
+struct SvdBufs {
+  double* sig2;
+  double* qn;
+  int* perm;
+  int* piv;
+};
+
+// Phase 1 of a two-site update of bond b: Phi = G (B_b B_{b+1}) and theta =
+// lam_{b-1} Phi, both row-major: row (al s1), column (s2 ga).  With `pre` the
+// product B_b B_{b+1} is given ([Dl][kD^2][Dr], the layout of theta itself,
+// so pre may be T: each item reads and writes only its own kD^2 entries).
+// Returns |theta|_F^2 (the same in every lane).
 template <int kD>
-__device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char* slot, int b, const double2* G,
-                                bool adjoint, bool record, bool count, WarpCtx& w, const double2* pre = nullptr) {
+__device__ double theta_build(const TrajParams& p, const Lay& Y, unsigned char* slot, int b, const double2* G,
+                              bool adjoint, WarpCtx& w, double2* T, double2* Phi, const double2* pre) {
   constexpr int kI = kD / 2;
   const int lane = w.lane;
-  const int chi = p.chi;
   const int lstride = Y.L.chi;
-  int* D = slot_dims(slot);
+  const int* D = slot_dims(slot);
   const int Dl = D[b], Dc = D[b + 1], Dr = D[b + 2];
-  const int m = kD * Dl, n = kD * Dr;
-  double2* sites = slot_sites(slot, Y.L);
-  double* lam = slot_lam(slot, Y.L);
-  double2* A = sites + Y.site_off[b];
-  double2* Bt = sites + Y.site_off[b + 1];
-  // theta (then R^dagger) and Phi in the warp's shared slab when they fit
-  double2* T = theta_home(p, kD * kD, m * n, w);
-  double2* Phi = (2 * m * n <= p.slab_elems) ? w.slab + m * n : w.scratch;
+  const int n = kD * Dr;
+  const double2* sites = slot_sites(slot, Y.L);
+  const double* lam = slot_lam(slot, Y.L);
+  const double2* A = sites + Y.site_off[b];
+  const double2* Bt = sites + Y.site_off[b + 1];
 
   double2 g[16];
 #pragma unroll
@@ -111,11 +121,6 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
 #pragma unroll
     for (int c = 0; c < 4; ++c) g[r * 4 + c] = adjoint ? cconj(G[c * 4 + r]) : G[r * 4 + c];
 
-  // Phase 1: Phi = G (B_b B_{b+1}) and theta, both row-major: row (al s1), column (s2 ga).
-  // With `pre` the product B_b B_{b+1} is given ([Dl][kD^2][Dr], the layout
-  // of theta itself, so pre may be T: each item reads and writes only its own
-  // kD^2 entries).
-  TNRC_TIC(t_c);
   double fro = 0.0;
   for (int it = lane; it < Dl * Dr; it += 32) {
     const int al = it / Dr, ga = it - al * Dr;
@@ -162,25 +167,29 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   }
   fro = warp_sum(fro);
   __syncwarp();
-  TNRC_TOC(w, 0, t_c);
+  return fro;
+}
 
-  // Phase 2: pivoted QR of theta, then one-sided Jacobi on the r columns of
-  // R^dagger (column j = conjugated row j of R, contiguous at T + j n).
-  TNRC_TIC(t_j);
-  const double zthr = kJacobiZero * kJacobiZero * fro;
-  int r = warp_qrcp(T, m, n, zthr, w.piv, w.qn, lane);
-  if (r < 1) r = 1;  // theta == 0 (or not finite): keep one column; the NaN check below reports it
-  for (int e = lane; e < r * n; e += 32) T[e] = cconj(T[e]);
-  __syncwarp();
-  TNRC_TOC(w, 1, t_j);
-  TNRC_TIC(t_s);
-  const int sw = warp_jacobi(T, n, r, fro, w.qn, lane);   // qn is free after the QR
-  TNRC_TOC(w, 8, t_s);
+// Phases 3 and 4 of a two-site update of bond b, after the SVD left R^dagger
+// V = Z S in T (r columns of length n; QR pivots in bf.piv): rank and
+// truncate, then lam_b <- S_k / |S_k|, B_{b+1} <- Y_k^dag, B_b <- Phi Y_k /
+// |S_k|, where Y[piv[c]][i] = Z[c][i] = T[perm[i] n + c] / sigma_i.
+template <int kD>
+__device__ void theta_finish(const TrajParams& p, const Lay& Y, unsigned char* slot, int b, double2* T,
+                             const double2* Phi, int r, int sw, bool record, bool count, WarpCtx& w, SvdBufs bf) {
+  const int lane = w.lane;
+  const int lstride = Y.L.chi;
+  int* D = slot_dims(slot);
+  const int Dl = D[b], Dc = D[b + 1], Dr = D[b + 2];
+  const int m = kD * Dl, n = kD * Dr;
+  double2* sites = slot_sites(slot, Y.L);
+  double* lam = slot_lam(slot, Y.L);
+  double2* A = sites + Y.site_off[b];
+  double2* Bt = sites + Y.site_off[b + 1];
 
-  // Phase 3: rank, truncate.
   TNRC_TIC(t_r);
   double kept2, tot2, gap;
-  int k = warp_rank_truncate(T, n, r, chi, p.eps, w.sig2, w.perm, lane, kept2, tot2, gap);
+  int k = warp_rank_truncate(T, n, r, p.chi, p.eps, bf.sig2, bf.perm, lane, kept2, tot2, gap);
   if (k > Y.dcap[b + 1]) {  // cannot happen (k <= min(m, n, chi)); keeps memory in bounds regardless
     k = Y.dcap[b + 1];
     if (lane == 0) atomicOr(p.status, kStatusBadDims);
@@ -206,26 +215,24 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   const double inv_kn = rsqrt(kept2);
   TNRC_TOC(w, 2, t_r);
 
-  // Phase 4: write lam_b, B_{b+1} = Y_k^dag, B_b = Phi Y_k / |S_k|, where
-  // Y[piv[c]][i] = Z[c][i] = T[perm[i] n + c] / sigma_i (1 / sigma_i once per
-  // kept value, in qn, which the Jacobi no longer needs).
+  // 1 / sigma once per kept value, in qn, which the Jacobi no longer needs
   TNRC_TIC(t_w);
   double* lamw = lam + (size_t)b * lstride;
-  const int* piv = w.piv;
-  double* isig = w.qn;
+  const int* piv = bf.piv;
+  double* isig = bf.qn;
   for (int i = lane; i < k; i += 32) {
-    lamw[i] = sqrt(w.sig2[w.perm[i]]) * inv_kn;
-    isig[i] = rsqrt(w.sig2[w.perm[i]]);
+    lamw[i] = sqrt(bf.sig2[bf.perm[i]]) * inv_kn;
+    isig[i] = rsqrt(bf.sig2[bf.perm[i]]);
   }
   __syncwarp();
   for (int it = lane; it < k * n; it += 32) {
     const int i = it / n, c = it - i * n;
-    const int j = w.perm[i];
+    const int j = bf.perm[i];
     Bt[(size_t)i * n + piv[c]] = cscale(cconj(T[(size_t)j * n + c]), isig[i]);
   }
   for (int it = lane; it < m * k; it += 32) {
     const int row = it / k, i = it - row * k;
-    const int j = w.perm[i];
+    const int j = bf.perm[i];
     const double2* ph = Phi + (size_t)row * n;
     const double2* z = T + (size_t)j * n;
     double2 acc = make_double2(0.0, 0.0);
@@ -236,6 +243,95 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   if (lane == 0) D[b + 1] = k;
   __syncwarp();
   TNRC_TOC(w, 3, t_w);
+}
+
+template <int kD>
+__device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char* slot, int b, const double2* G,
+                                bool adjoint, bool record, bool count, WarpCtx& w, const double2* pre = nullptr) {
+  const int lane = w.lane;
+  const int* D = slot_dims(slot);
+  const int m = kD * D[b], n = kD * D[b + 2];
+  // theta (then R^dagger) and Phi in the warp's shared slab when they fit
+  double2* T = theta_home(p, kD * kD, m * n, w);
+  double2* Phi = (2 * m * n <= p.slab_elems) ? w.slab + m * n : w.scratch;
+  TNRC_TIC(t_c);
+  const double fro = theta_build<kD>(p, Y, slot, b, G, adjoint, w, T, Phi, pre);
+  TNRC_TOC(w, 0, t_c);
+
+  // Phase 2: pivoted QR of theta, then one-sided Jacobi on the r columns of
+  // R^dagger (column j = conjugated row j of R, contiguous at T + j n).
+  TNRC_TIC(t_j);
+  const double zthr = kJacobiZero * kJacobiZero * fro;
+  int r = warp_qrcp(T, m, n, zthr, w.piv, w.qn, lane);
+  if (r < 1) r = 1;  // theta == 0 (or not finite): keep one column; the NaN check reports it
+  for (int e = lane; e < r * n; e += 32) T[e] = cconj(T[e]);
+  __syncwarp();
+  TNRC_TOC(w, 1, t_j);
+  TNRC_TIC(t_s);
+  const int sw = warp_jacobi(T, n, r, fro, w.qn, lane);   // qn is free after the QR
+  TNRC_TOC(w, 8, t_s);
+  theta_finish<kD>(p, Y, slot, b, T, Phi, r, sw, record, count, w, SvdBufs{w.sig2, w.qn, w.perm, w.piv});
+}
+
+// Whether bonds b1 and b2 of one layer can be updated as a pair: both thetas
+// and both Phis fit the warp's shared slab side by side, and every side is
+// at most 64 (the per-warp SVD arrays are split in halves).
+template <int kD>
+__device__ __forceinline__ bool pair_fits(const TrajParams& p, const int* D, int b1, int b2) {
+  const int m1 = kD * D[b1], n1 = kD * D[b1 + 2], m2 = kD * D[b2], n2 = kD * D[b2 + 2];
+  return 2 * (m1 * n1 + m2 * n2) <= p.slab_elems && m1 <= 64 && n1 <= 64 && m2 <= 64 && n2 <= 64;
+}
+
+// Where a pair update keeps its two thetas in the slab: T1 at 0, Phi1 at
+// m1 n1, T2 at 2 m1 n1, Phi2 after T2.
+template <int kD>
+__device__ __forceinline__ double2* pair_theta(const TrajParams& p, const int* D, int b1, int which, WarpCtx& w) {
+  const int mn1 = kD * D[b1] * kD * D[b1 + 2];
+  return which == 0 ? w.slab : w.slab + 2 * mn1;
+}
+
+// Two two-site updates (bonds b1, b2 of one layer, disjoint sites) by one
+// warp: thetas built one after the other, then the pivoted QR and the Jacobi
+// of both at once on the two half-warps, then ranks and splits one after the
+// other.  The same arithmetic per bond as two_site_update, in another lane
+// arrangement (so the same results up to the order of sums).
+template <int kD>
+__device__ void two_site_update_pair(const TrajParams& p, const Lay& Y, unsigned char* slot, int b1,
+                                     const double2* G1, int b2, const double2* G2, bool adjoint, bool record,
+                                     bool count, WarpCtx& w, const double2* pre1 = nullptr,
+                                     const double2* pre2 = nullptr) {
+  const int lane = w.lane;
+  const int* D = slot_dims(slot);
+  const int m1 = kD * D[b1], n1 = kD * D[b1 + 2], m2 = kD * D[b2], n2 = kD * D[b2 + 2];
+  double2* T1 = w.slab;
+  double2* Phi1 = w.slab + m1 * n1;
+  double2* T2 = w.slab + 2 * m1 * n1;
+  double2* Phi2 = T2 + m2 * n2;
+  TNRC_TIC(t_c);
+  const double fro1 = theta_build<kD>(p, Y, slot, b1, G1, adjoint, w, T1, Phi1, pre1);
+  const double fro2 = theta_build<kD>(p, Y, slot, b2, G2, adjoint, w, T2, Phi2, pre2);
+  TNRC_TOC(w, 0, t_c);
+  const SvdBufs bf1{w.sig2, w.qn, w.perm, w.piv};
+  const SvdBufs bf2{w.sig2 + 64, w.qn + 64, w.perm + 64, w.piv + 64};
+  const bool hi = lane >= 16;
+  TNRC_TIC(t_j);
+  int rh = half_qrcp(hi ? T2 : T1, hi ? m2 : m1, hi ? n2 : n1,
+                     kJacobiZero * kJacobiZero * (hi ? fro2 : fro1), hi ? bf2.piv : bf1.piv,
+                     hi ? bf2.qn : bf1.qn, lane);
+  int r1 = __shfl_sync(0xffffffffu, rh, 0), r2 = __shfl_sync(0xffffffffu, rh, 16);
+  if (r1 < 1) r1 = 1;
+  if (r2 < 1) r2 = 1;
+  for (int e = lane; e < r1 * n1; e += 32) T1[e] = cconj(T1[e]);
+  for (int e = lane; e < r2 * n2; e += 32) T2[e] = cconj(T2[e]);
+  __syncwarp();
+  TNRC_TOC(w, 1, t_j);
+  TNRC_TIC(t_s);
+  const int swh = half_jacobi(hi ? T2 : T1, hi ? n2 : n1, hi ? r2 : r1, hi ? fro2 : fro1, hi ? bf2.qn : bf1.qn,
+                              lane);
+  const int sw1 = __shfl_sync(0xffffffffu, swh, 0), sw2 = __shfl_sync(0xffffffffu, swh, 16);
+  TNRC_TOC(w, 8, t_s);
+  theta_finish<kD>(p, Y, slot, b1, T1, Phi1, r1, sw1, record, count, w, bf1);
+  theta_finish<kD>(p, Y, slot, b2, T2, Phi2, r2, sw2, record, count, w, bf2);
 }
 
 // ---------------------------------------------------------------------------
@@ -472,11 +568,13 @@ __device__ void bond_gradient(const TrajParams& p, const Lay& Y, const unsigned 
   w.alg += 8ull * dcl * (kD * dam * dal + kDD * dar * dam + kDD * dcr * dar +
                          (unsigned long long)kDD * kDD * dcr) + 2048ull;
   // Wc = c_b c_{b+1} [dcl][kD^2][dcr] at Wc (theta's home); the other three
-  // intermediates packed at their actual sizes after it in the warp's shared
-  // slab when everything fits, else in its global scratch past theta's room
+  // intermediates packed at their actual sizes right after it in the warp's
+  // shared slab when they fit there, else in its global scratch past theta's
+  // room
   const int n1 = dcl * kD * dam, n2 = dcl * kDD * dar, n3 = dcl * kDD * dcr;
-  double2* U1 = (Wc == w.slab && n3 + n1 + n2 + n3 <= p.slab_elems)
-                    ? w.slab + n3
+  const bool wc_in_slab = Wc >= w.slab && Wc < w.slab + p.slab_elems;
+  double2* U1 = (wc_in_slab && (Wc - w.slab) + n3 + n1 + n2 + n3 <= p.slab_elems)
+                    ? Wc + n3
                     : w.scratch + (size_t)2 * kDD * chi * chi;   // [dcl][kD][dam]
   double2* U2 = U1 + n1;                          // [dcl][kD^2][dar]
   double2* U3 = U2 + n2;                          // [dcl][kD^2][dcr]
@@ -591,6 +689,25 @@ __device__ int copy_slot(const TrajParams& p, const Lay& Ys, const unsigned char
   return 0;
 }
 
+// Entries e and e+1 of the layer's bond order (w.order, nb entries): one
+// warp updates both, as a pair when both are small (two_site_update_pair),
+// else one after the other.  The grouping depends only on the order and the
+// bond dimensions, not on which warp or CTA takes it, so every launch form
+// computes the same thing.
+template <int kD>
+__device__ void forward_group(const TrajParams& p, const Lay& Y, unsigned char* slot, int s, int l, int e, int nb,
+                              bool adjoint, bool record, bool count, WarpCtx& w) {
+  const int b1 = w.order[e];
+  const int b2 = (e + 1 < nb) ? w.order[e + 1] : -1;
+  if (b2 >= 0 && pair_fits<kD>(p, slot_dims(slot), b1, b2)) {
+    two_site_update_pair<kD>(p, Y, slot, b1, layer_rec(p, s, l, b1).G, b2, layer_rec(p, s, l, b2).G, adjoint,
+                             record, count, w);
+    return;
+  }
+  two_site_update<kD>(p, Y, slot, b1, layer_rec(p, s, l, b1).G, adjoint, record, count, w);
+  if (b2 >= 0) two_site_update<kD>(p, Y, slot, b2, layer_rec(p, s, l, b2).G, adjoint, record, count, w);
+}
+
 // All bonds of truncated layer l.  The warps take bonds from a shared counter
 // in decreasing order of cost (largest SVD first), so that they reach the
 // layer barrier together; a bond's result does not depend on which warp
@@ -603,17 +720,44 @@ __device__ void apply_layer(const TrajParams& p, const Lay& Y, unsigned char* sl
   const int lane = w.lane;
   if (warp == 0) order_layer(p, slot_dims(slot), parity, w);
   __syncthreads();
-  for (;;) {
-    int j = 0;
-    if (lane == 0) j = atomicAdd(w.next, 1);
-    j = __shfl_sync(0xffffffffu, j, 0);
-    if (j >= nb) break;
-    const int b = w.order[j];
-    two_site_update<kD>(p, Y, slot, b, layer_rec(p, s, l, b).G, adjoint, record, count, w);
+  for (;;) {   // two bonds at a time
+    int e = 0;
+    if (lane == 0) e = atomicAdd(w.next, 2);
+    e = __shfl_sync(0xffffffffu, e, 0);
+    if (e >= nb) break;
+    forward_group<kD>(p, Y, slot, s, l, e, nb, adjoint, record, count, w);
   }
   TNRC_TIC(t_b);
   __syncthreads();
   TNRC_TOC(w, 7, t_b);
+}
+
+// Entries e and e+1 of the layer's bond order: each bond's gradient and its
+// costate update, the two updates as a pair when both bonds are small (the
+// grouping rule of forward_group).
+template <int kD>
+__device__ void costate_group(const TrajParams& p, const Lay& Y, unsigned char* cslot, const StateView av, int s,
+                              int l, int e, int nb, double2 wO, double* gsp_row, WarpCtx& w) {
+  constexpr int kDD = kD * kD;
+  const int* Dc = slot_dims(cslot);
+  const int b1 = w.order[e];
+  const int b2 = (e + 1 < nb) ? w.order[e + 1] : -1;
+  if (b2 >= 0 && pair_fits<kD>(p, Dc, b1, b2)) {
+    double2* th1 = pair_theta<kD>(p, Dc, b1, 0, w);
+    double2* th2 = pair_theta<kD>(p, Dc, b1, 1, w);
+    bond_gradient<kD>(p, Y, cslot, av, s, l, b1, wO, gsp_row, w, th1);
+    bond_gradient<kD>(p, Y, cslot, av, s, l, b2, wO, gsp_row, w, th2);
+    two_site_update_pair<kD>(p, Y, cslot, b1, layer_rec(p, s, l, b1).G, b2, layer_rec(p, s, l, b2).G, true, false,
+                             true, w, th1, th2);
+    return;
+  }
+  for (int q = 0; q < 2; ++q) {
+    const int b = q == 0 ? b1 : b2;
+    if (b < 0) break;
+    double2* th = theta_home(p, kDD, kDD * Dc[b] * Dc[b + 2], w);
+    bond_gradient<kD>(p, Y, cslot, av, s, l, b, wO, gsp_row, w, th);
+    two_site_update<kD>(p, Y, cslot, b, layer_rec(p, s, l, b).G, true, false, true, w, th);
+  }
 }
 
 // One layer of the costate sweep (App. A): the environments of <c_l|.|a_l>
@@ -643,15 +787,12 @@ __device__ void costate_layer(const TrajParams& p, const Lay& Y, unsigned char* 
   __syncthreads();
   layer_envs<kD>(p, Y, cslot, av, w, warp);
   __syncthreads();
-  for (;;) {
-    int j = 0;
-    if (lane == 0) j = atomicAdd(w.next, 1);
-    j = __shfl_sync(0xffffffffu, j, 0);
-    if (j >= nb) break;
-    const int b = w.order[j];
-    double2* th = theta_home(p, kDD, kDD * Dc[b] * Dc[b + 2], w);
-    bond_gradient<kD>(p, Y, cslot, av, s, l, b, wO, gsp_row, w, th);
-    two_site_update<kD>(p, Y, cslot, b, layer_rec(p, s, l, b).G, true, false, true, w, th);
+  for (;;) {   // two bonds at a time
+    int e = 0;
+    if (lane == 0) e = atomicAdd(w.next, 2);
+    e = __shfl_sync(0xffffffffu, e, 0);
+    if (e >= nb) break;
+    costate_group<kD>(p, Y, cslot, av, s, l, e, nb, wO, gsp_row, w);
   }
   TNRC_TIC(t_b);
   __syncthreads();
@@ -910,14 +1051,19 @@ __global__ void plain_copy_kernel(TrajParams p, const unsigned char* src, unsign
   copy_slot<kD>(p, p.full, src, p.full, dst);
 }
 
-// Forward layer l of trajectory (s, .) on `slot`: CTA j updates the j-th bond.
+// Forward layer l of trajectory (s, .) on `slot`: CTA j updates the j-th
+// group of two bonds of the layer's bond order (the grouping of the batched
+// launch, so the results are the same).
 template <int kD>
 __global__ void __launch_bounds__(32) plain_fwd_kernel(TrajParams p, unsigned char* slot, int s, int l) {
-  __shared__ int s_order[1], s_next;
+  __shared__ int s_order[128], s_next;
   WarpCtx w;
   plain_warp(p, w, blockIdx.x, s_order, &s_next, 0);
-  const int b = layer_parity(p, l) + 2 * (int)blockIdx.x;
-  two_site_update<kD>(p, p.full, slot, b, layer_rec(p, s, l, b).G, false, true, true, w);
+  const int parity = layer_parity(p, l);
+  const int nb = (p.N - 1 - parity + 1) / 2;
+  order_layer(p, slot_dims(slot), parity, w);   // reads outer bond dimensions only, which no update changes
+  __syncwarp();
+  forward_group<kD>(p, p.full, slot, s, l, 2 * (int)blockIdx.x, nb, false, true, true, w);
   if (w.lane == 0) atomicAdd(&p.counters[1], (unsigned long long)w.sweeps);
 }
 
@@ -949,19 +1095,20 @@ __global__ void __launch_bounds__(64) plain_envs_kernel(TrajParams p, const unsi
   layer_envs<kD>(p, p.full, cslot, slot_view(aslot, p.full), w, warp);
 }
 
-// Gradient and costate update of the bonds of layer l (CTA j: the j-th bond).
+// Gradient and costate update of the bonds of layer l (CTA j: the j-th
+// group of two bonds, as in the batched launch).
 template <int kD>
 __global__ void __launch_bounds__(32) plain_bwd_kernel(TrajParams p, unsigned char* cslot, const unsigned char* aslot,
                                                        int s, int l, int t) {
-  __shared__ int s_order[1], s_next;
+  __shared__ int s_order[128], s_next;
   WarpCtx w;
   plain_warp(p, w, blockIdx.x, s_order, &s_next, 0);
-  const int b = layer_parity(p, l) + 2 * (int)blockIdx.x;
-  const int* Dc = slot_dims(cslot);
-  double2* th = theta_home(p, kD * kD, kD * kD * Dc[b] * Dc[b + 2], w);
-  bond_gradient<kD>(p, p.full, cslot, slot_view(aslot, p.full), s, l, b, p.O[t],
-                    p.gsp + (size_t)t * p.K * p.C * p.N, w, th);
-  two_site_update<kD>(p, p.full, cslot, b, layer_rec(p, s, l, b).G, true, false, true, w, th);
+  const int parity = layer_parity(p, l);
+  const int nb = (p.N - 1 - parity + 1) / 2;
+  order_layer(p, slot_dims(cslot), parity, w);
+  __syncwarp();
+  costate_group<kD>(p, p.full, cslot, slot_view(aslot, p.full), s, l, 2 * (int)blockIdx.x, nb, p.O[t],
+                    p.gsp + (size_t)t * p.K * p.C * p.N, w);
   if (w.lane == 0) atomicAdd(&p.counters[1], (unsigned long long)w.sweeps);
 }
 
@@ -973,6 +1120,7 @@ extern "C" cudaError_t tnrc_launch_plain(const tnrc::TrajParams* p, int op, cons
                                          unsigned char* b, int s, int l, int t, size_t smem, cudaStream_t st) {
   (void)cudaGetLastError();
   const int nb = (p->N - 1 - ((l + p->first_parity) & 1) + 1) / 2;
+  const int ng = (nb + 1) / 2;   // groups of two bonds
   const bool d4 = p->phys_dim == 4;
   switch (op) {
     case 0:
@@ -980,8 +1128,8 @@ extern "C" cudaError_t tnrc_launch_plain(const tnrc::TrajParams* p, int op, cons
       else tnrc::plain_copy_kernel<2><<<1, 256, 0, st>>>(*p, a, b);
       break;
     case 1:
-      if (d4) tnrc::plain_fwd_kernel<4><<<nb, 32, smem, st>>>(*p, b, s, l);
-      else tnrc::plain_fwd_kernel<2><<<nb, 32, smem, st>>>(*p, b, s, l);
+      if (d4) tnrc::plain_fwd_kernel<4><<<ng, 32, smem, st>>>(*p, b, s, l);
+      else tnrc::plain_fwd_kernel<2><<<ng, 32, smem, st>>>(*p, b, s, l);
       break;
     case 2:
       if (d4) tnrc::plain_overlap_kernel<4><<<1, 32, smem, st>>>(*p, a, b, t);
@@ -992,8 +1140,8 @@ extern "C" cudaError_t tnrc_launch_plain(const tnrc::TrajParams* p, int op, cons
       else tnrc::plain_envs_kernel<2><<<1, 64, smem, st>>>(*p, b, a);
       break;
     case 4:
-      if (d4) tnrc::plain_bwd_kernel<4><<<nb, 32, smem, st>>>(*p, b, a, s, l, t);
-      else tnrc::plain_bwd_kernel<2><<<nb, 32, smem, st>>>(*p, b, a, s, l, t);
+      if (d4) tnrc::plain_bwd_kernel<4><<<ng, 32, smem, st>>>(*p, b, a, s, l, t);
+      else tnrc::plain_bwd_kernel<2><<<ng, 32, smem, st>>>(*p, b, a, s, l, t);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -1003,7 +1151,7 @@ extern "C" cudaError_t tnrc_launch_plain(const tnrc::TrajParams* p, int op, cons
 
 extern "C" cudaError_t tnrc_plain_prepare() {
   cudaError_t e = cudaSuccess;
-  const int lim = 200 * 1024;
+  const int lim = 226 * 1024;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(tnrc::plain_fwd_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(tnrc::plain_fwd_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(tnrc::plain_overlap_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);

@@ -4,9 +4,12 @@ Each request asks for F (and optionally dF/du) of one problem -- chain length,
 chi_max, slices, ensemble, inputs/targets -- at one control vector, with its
 own noise seed.  The server
 
-  * keeps one tnrc context per problem resident on the device (canonical
-    inputs/targets, gate tables, MPS and costate working slots) and reuses it
-    for every later request of that problem, as an optimiser's iterations do;
+  * keeps tnrc contexts resident on the device (canonical inputs/targets,
+    gate tables, MPS and costate working slots) and reuses them for every
+    later request of their problem, as an optimiser's iterations do; a
+    request for a problem whose resident contexts are all busy gets another
+    resident copy (made once, then reused like the first), so one problem
+    can have several requests in flight;
   * admits a request when its context's device footprint fits the memory
     budget next to the contexts already holding work (idle contexts are
     destroyed first, least recently used, when memory is short);
@@ -65,6 +68,7 @@ class Request:
     operator: bool = False        # evolve the operator from the identity (gate objective)
     # filled by the server
     priority: str = ""
+    device_s: float = 0.0         # device span of the evaluation (CUDA events on its stream)
     arrival: float = 0.0
     start: float = 0.0
     finish: float = 0.0
@@ -137,6 +141,7 @@ class _Slot:
         self.ctx.sync()
         span = self.ev0.elapsed_time(self.event) / 1000.0
         self.service = span if self.service is None else min(self.service, span)
+        req.device_s = span
         req.F = float(self.F.item())
         req.grad = self.g.cpu().numpy().copy() if req.want_grad else None
         self.busy = None
@@ -167,6 +172,7 @@ class Server:
         self.mem_budget = mem_budget
         self.max_inflight = max_inflight
         self.short_s = short_s
+        self.key_service: dict = {}
         self.pending = collections.deque()
         self.slots: list = []
         self.done: list = []
@@ -225,9 +231,12 @@ class Server:
         self.slots.remove(slot)
 
     def _service(self, key):
-        """Shortest device span measured for this problem (s), or None."""
+        """Shortest device span measured for this problem (s), or None; kept
+        per problem, so that a new resident copy of it inherits the estimate."""
         known = [s.service for s in self.slots if s.key == key and s.service is not None]
-        return min(known) if known else None
+        if known:
+            self.key_service[key] = min(known + ([self.key_service[key]] if key in self.key_service else []))
+        return self.key_service.get(key)
 
     def _next_pending(self) -> Request:
         """The pending request to admit next: the one whose problem has the
@@ -268,7 +277,8 @@ class Server:
                 slot = _Slot(req, self.device)
             self.slots.append(slot)
         req.start = time.perf_counter()
-        slot.launch(req, high=slot.service is not None and slot.service <= self.short_s)
+        t = self._service(req.key)
+        slot.launch(req, high=t is not None and t <= self.short_s)
         self.admitted += 1
         return True
 
