@@ -10,6 +10,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/tnrc.h"
 #include "plan.h"
 #include "tnrc_device.cuh"
@@ -32,6 +34,15 @@ extern "C" cudaError_t tnrc_launch_reduce(const double2* O, int T, double* F, do
 extern "C" cudaError_t tnrc_launch_canon(const tnrc::CanonArgs* a, int nmps, cudaStream_t st);
 
 using namespace tnrc_host;
+
+namespace {
+// An NVTX range over a host-side phase (launches are asynchronous, so a range
+// marks when the phase was issued); a no-op unless a profiler is attached.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+}  // namespace
 
 struct tnrc_ctx {
   Plan plan;
@@ -140,7 +151,9 @@ tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, dou
   cudaStream_t st = ctx->stream;
   if (!capturing) CK(cudaEventRecord(ctx->ev0, st));
   ctx->timed_last = !capturing;
+  Range eval_range(grad ? "tnrc:evaluate(F, grad)" : "tnrc:evaluate(F)");
   if (ctx->gates_dirty) {
+    Range r("tnrc:layer gates");
     CK(tnrc_launch_layer_gates(P.N, P.K, P.C, P.M, P.terms, P.order, P.nsub, P.n_layers, P.recs, P.first_parity,
                                ctx->dt, ctx->at<double>(P.off_u), ctx->at<unsigned char>(P.off_mask),
                                ctx->at<double>(P.off_gfix), ctx->at<double>(P.off_J), ctx->at<int>(P.off_loff),
@@ -163,12 +176,16 @@ tnrc_status launch_eval(tnrc_ctx* ctx, bool grad, double* dF, double* dgrad, dou
   }
   const bool timed = !capturing && ctx->tev_used + 2 <= ctx->tev.size();
   if (timed) CK(cudaEventRecord(ctx->tev[ctx->tev_used], st));
-  CK(tnrc_launch_traj(&tp, grid, smem, st));
+  {
+    Range r("tnrc:trajectories");
+    CK(tnrc_launch_traj(&tp, grid, smem, st));
+  }
   if (timed) {
     CK(cudaEventRecord(ctx->tev[ctx->tev_used + 1], st));
     ctx->tev_used += 2;
   }
   const int X = P.K * P.C * P.N;
+  Range red_range("tnrc:reduce");
   CK(tnrc_launch_reduce(ctx->at<double2>(P.off_O), P.T, dF ? dF : ctx->at<double>(P.off_F), dper,
                         grad ? ctx->at<double>(P.off_gsp) : nullptr, X,
                         grad ? (dgrad ? dgrad : ctx->at<double>(P.off_grad)) : nullptr, st));
@@ -312,6 +329,7 @@ tnrc_status tnrc_create(const tnrc_problem* pb, const tnrc_mps* inputs, const tn
     return bail(TNRC_E_CUDA);
   // canonical inputs and targets
   {
+    Range r("tnrc:canonical inputs and targets");
     const int nmps = 2 * P.P;
     std::vector<int> dims((size_t)nmps * (N + 1));
     std::vector<long long> offs(nmps);
@@ -509,6 +527,7 @@ tnrc_status tnrc_fidelity_grad_plain(tnrc_ctx* ctx, double* F, double* grad) {
   const unsigned char* tg = ctx->at<unsigned char>(P.off_tg);
   const int64_t KCN = (int64_t)P.K * P.C * P.N;
   CK(cudaEventRecord(ctx->ev0, st));
+  Range plain_range("tnrc:plain path");
   for (int t = 0; t < P.T; ++t) {
     const int s = t / P.P, pi = t - s * P.P;
     CK(tnrc_launch_plain(&tp, 0, in + (size_t)pi * sb, hist, 0, 0, 0, 0, st));
