@@ -243,6 +243,8 @@ def gpu_arm(args, w):
     tuned = autotune.lookup(w.N, w.K, w.chi, w.M, w.P, w.C, grad=True, operator=w.operator)
     ctx = Context(w.N, w.K, w.dt, w.chi, w.M, w.C, ins, tgs, cutoff=w.sv_cutoff, mask=mask,
                   stream=stream.cuda_stream, warps=tuned[0], ctas_per_sm=tuned[1], **form_kwargs(w))
+    pairs = autotune.lookup_pairs(w.N, w.K, w.chi, w.M, w.P, w.C, grad=True, operator=w.operator)
+    ctx.set_svd_shape(pairs)
     u_dev = torch.tensor(u, dtype=torch.float64, device=dev)
     F_dev = torch.zeros(1, dtype=torch.float64, device=dev)
     g_dev = torch.zeros(u.shape, dtype=torch.float64, device=dev)
@@ -350,6 +352,7 @@ def gpu_arm(args, w):
         # reduce_grad_kernel (the launch list under profiles/ shows the same five)
         "gpu_launches": 5 * args.steps,
         "launch_shape": {"warps_per_cta": tuned[0] or "default", "ctas_per_sm": tuned[1] or 1,
+                         "svd": "two per warp (half-warps)" if pairs else "one per warp",
                          "source": "autotune cache" if tuned[0] else "default"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -601,6 +604,8 @@ def plain_arm(args, w):
                               mask=ws.mask(), warps=tuned[0], ctas_per_sm=tuned[1], **form_kwargs(ws))
             finally:
                 os.environ.pop("TNRC_GRID", None)
+            ctx.set_svd_shape(autotune.lookup_pairs(w.N, w.K, w.chi, w.M, w.P, w.C, grad=True,
+                                                    operator=w.operator))
             ctx.set_controls(ws.controls())
             ctx.sample_noise(ws.seed_J, ws.noise_dist, ws.noise_scale)
             run = ctx.fidelity_grad_plain if mode == "plain" else ctx.fidelity_grad

@@ -223,6 +223,16 @@ tnrc_status tnrc_set_graphs(tnrc_ctx* ctx, int32_t enable);
  * tnrc_fidelity_grad, and TNRC_E_NOMEM. */
 tnrc_status tnrc_fidelity_grad_plain(tnrc_ctx* ctx, double* F, double* grad);
 
+/* Matrix shape of the trajectory kernel's SVDs: pairs = 1 (the default) lets
+ * a warp take two small two-site updates at once, their pivoted QR and
+ * Jacobi SVDs running on the two half-warps (when both thetas and both Phis
+ * fit the warp's shared slab and no side exceeds 64), so the per-round
+ * scalar work of the Jacobi is shared by two matrices; pairs = 0 gives every
+ * SVD a whole warp.  Results agree within rounding (the sums run in another
+ * lane arrangement); the plain path follows the same setting.  Captured
+ * graphs are dropped when it changes.  The autotuner picks it per shape. */
+tnrc_status tnrc_set_svd_shape(tnrc_ctx* ctx, int32_t pairs);
+
 /* Order the context's later work on another stream (a cudaStream_t; NULL =
  * the legacy default stream, refused while graphs are on).  Waits for the
  * work already queued on the current stream first.  A serving loop uses it

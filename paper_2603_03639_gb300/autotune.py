@@ -1,13 +1,13 @@
 """Launch-shape autotuner for the trajectory kernel.
 
 The kernel runs one trajectory per CTA; within a CTA the warps share the
-disjoint bonds of a TEBD layer (one warp per two-site SVD at a time).  The
-free choices are the warps per CTA (how many bonds of a layer run at once,
-and how evenly a layer's bonds divide among them) and the resident CTAs per
-SM (how many trajectories interleave on an SM; the register file holds 8 of
-this kernel's warps per SM).  The tuner times each candidate on the actual
-problem with CUDA events around the kernel and caches the fastest per shape
-bucket in a JSON file.
+disjoint bonds of a TEBD layer.  The free choices are the warps per CTA (how
+many bonds of a layer run at once, and how evenly a layer's bonds divide
+among them), the resident CTAs per SM (how many trajectories interleave on an
+SM; the register file holds 8 of this kernel's warps per SM) and the matrix
+shape (two small SVDs per warp on the half-warps, or one SVD per warp).  The
+tuner times each candidate on the actual problem with CUDA events around the
+kernel and caches the fastest per shape bucket in a JSON file.
 
     python -m paper_2603_03639_gb300.autotune --workload cnot50 --out tuned.json
 """
@@ -57,22 +57,37 @@ def lookup(N, K, chi, M, P, C, grad=True, path=None, operator=False):
     return (int(e["warps"]), int(e["ctas_per_sm"])) if e else (0, 0)
 
 
+def lookup_pairs(N, K, chi, M, P, C, grad=True, path=None, operator=False):
+    """The cached matrix shape for this problem: True = two small SVDs per warp
+    on the half-warps (also the default when nothing is cached), False = one
+    SVD per warp."""
+    cache = load(path)
+    key = shape_key(N, K, chi, M, P, C, grad, operator)
+    e = cache.get(key)
+    if e is None:
+        w, c = lookup(N, K, chi, M, P, C, grad, path, operator)
+        e = next((v for v in cache.values() if v.get("warps") == w and v.get("ctas_per_sm") == c
+                  and v.get("operator", False) == operator), None)
+    return bool(e.get("pairs", True)) if e else True
+
+
 def tune(N, K, dt, chi, M, C, inputs, targets, u, noise, mask=None, grad=True, candidates=CANDIDATES, reps=1,
          stream=None, form=None):
-    """Time every candidate; returns (best (warps, ctas), {candidate: ms}).
-    form: Context keywords of the time discretisation and form (crosstalk,
-    order, substeps, operator)."""
+    """Time every launch shape with paired SVDs, then the two fastest with one
+    SVD per warp as well; returns (best (warps, ctas, pairs), {(warps, ctas,
+    pairs): ms}).  form: Context keywords of the time discretisation and form
+    (crosstalk, order, substeps, operator)."""
     from .tnrc import Context
     seed, dist, scale = noise
     form = form or {}
     nb = max((N - 1 + 1) // 2, 1)
     max_warps_per_sm = 8 if form.get("operator") else 16   # operators run the 255-register build only
     times = {}
-    for w, c in candidates:
-        if w * c > max_warps_per_sm or w > max(2, nb):
-            continue
+
+    def run(w, c, pairs):
         with Context(N, K, dt, chi, M, C, inputs, targets, mask=mask, stream=stream, warps=w, ctas_per_sm=c,
                      **form) as ctx:
+            ctx.set_svd_shape(pairs)
             ctx.set_controls(u)
             ctx.sample_noise(seed, dist, scale)
             (ctx.fidelity_grad if grad else ctx.fidelity)()          # warm-up
@@ -80,7 +95,14 @@ def tune(N, K, dt, chi, M, C, inputs, targets, u, noise, mask=None, grad=True, c
             for _ in range(reps):
                 (ctx.fidelity_grad if grad else ctx.fidelity)()
             st = ctx.stats()
-            times[(w, c)] = st["traj_ms"] / max(1, st["traj_launches"])
+            times[(w, c, pairs)] = st["traj_ms"] / max(1, st["traj_launches"])
+
+    for w, c in candidates:
+        if w * c > max_warps_per_sm or w > max(2, nb):
+            continue
+        run(w, c, True)
+    for w, c, _ in sorted(times, key=times.get)[:2]:
+        run(w, c, False)
     best = min(times, key=times.get)
     return best, times
 
@@ -108,11 +130,12 @@ def main():
                              "operator": w.operator})
     cache = load(args.out)
     key = shape_key(w.N, w.K, w.chi, w.M, w.P, w.C, grad, w.operator)
-    cache[key] = {"warps": best[0], "ctas_per_sm": best[1], "workload": w.name,
-                  "ms": {"%dx%d" % k: round(v, 3) for k, v in times.items()}}
+    name = lambda k: "%dx%d%s" % (k[0], k[1], "" if k[2] else "-warp")  # noqa: E731
+    cache[key] = {"warps": best[0], "ctas_per_sm": best[1], "pairs": bool(best[2]), "workload": w.name,
+                  "operator": bool(w.operator), "ms": {name(k): round(v, 3) for k, v in times.items()}}
     with open(args.out, "w") as f:
         json.dump(cache, f, indent=1, sort_keys=True)
-    print(json.dumps({"key": key, "best": best, "ms": {"%dx%d" % k: v for k, v in times.items()}}))
+    print(json.dumps({"key": key, "best": name(best), "ms": {name(k): v for k, v in times.items()}}))
 
 
 if __name__ == "__main__":

@@ -69,6 +69,7 @@ struct tnrc_ctx {
   // the dynamic shared memory that keeps the resident CTAs within the pool
   bool pooled = false;
   size_t pooled_smem = 0;
+  int pair_svd = 1;               // matrix shape: two small SVDs per warp (1) or one (0)
   bool timed_last = false;        // ev0/ev1 bracket the last evaluation (not a graph replay)
   std::vector<GraphEntry> graphs;
   char err[256] = {0};            // the CUDA failure that made the context unusable
@@ -143,6 +144,7 @@ tnrc::TrajParams traj_params(tnrc_ctx* ctx, bool grad) {
   tp.counters = ctx->at<unsigned long long>(P.off_counters);
   tp.status = ctx->at<int>(P.off_status);
   tp.work_counter = ctx->at<int>(P.off_wc);
+  tp.pair_svd = ctx->pair_svd;
   return tp;
 }
 
@@ -552,6 +554,17 @@ tnrc_status tnrc_fidelity_grad_plain(tnrc_ctx* ctx, double* F, double* grad) {
   if (r != TNRC_OK) return r;
   CK(cudaMemcpy(F, ctx->at<double>(P.off_F), 8, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(grad, ctx->at<double>(P.off_grad), (size_t)KCN * 8, cudaMemcpyDeviceToHost));
+  return TNRC_OK;
+}
+
+tnrc_status tnrc_set_svd_shape(tnrc_ctx* ctx, int32_t pairs) {
+  if (!ctx || (pairs != 0 && pairs != 1)) return TNRC_E_INVALID;
+  if (ctx->broken) return TNRC_E_CUDA;
+  if (ctx->pair_svd != pairs) {
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);   // captured with the other shape
+    ctx->graphs.clear();
+  }
+  ctx->pair_svd = pairs;
   return TNRC_OK;
 }
 

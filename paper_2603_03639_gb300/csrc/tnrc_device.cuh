@@ -126,6 +126,7 @@ struct TrajParams {
   // 1 = pooled (one CTA per trajectory, t = blockIdx.x; the CTA holds one of
   // n_regions work regions from region_owner while it runs, so the block
   // scheduler can interleave CTAs of other launches between trajectories)
+  int pair_svd;                    // 1: two small SVDs per warp on the half-warps (see traj.cu)
   int pooled;
   int n_regions;
   int* region_owner;               // [n_regions], 0 = free

@@ -273,13 +273,15 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   theta_finish<kD>(p, Y, slot, b, T, Phi, r, sw, record, count, w, SvdBufs{w.sig2, w.qn, w.perm, w.piv});
 }
 
-// Whether bonds b1 and b2 of one layer can be updated as a pair: both thetas
-// and both Phis fit the warp's shared slab side by side, and every side is
-// at most 64 (the per-warp SVD arrays are split in halves).
+// Whether bonds b1 and b2 of one layer are updated as a pair: pairing is on
+// for the context (the matrix shape the autotuner picks), both thetas and
+// both Phis fit the warp's shared slab side by side, and every side is at
+// most 64 (the per-warp SVD arrays are split in halves).
 template <int kD>
 __device__ __forceinline__ bool pair_fits(const TrajParams& p, const int* D, int b1, int b2) {
   const int m1 = kD * D[b1], n1 = kD * D[b1 + 2], m2 = kD * D[b2], n2 = kD * D[b2 + 2];
-  return 2 * (m1 * n1 + m2 * n2) <= p.slab_elems && m1 <= 64 && n1 <= 64 && m2 <= 64 && n2 <= 64;
+  return p.pair_svd && 2 * (m1 * n1 + m2 * n2) <= p.slab_elems && m1 <= 64 && n1 <= 64 && m2 <= 64 &&
+         n2 <= 64;
 }
 
 // Where a pair update keeps its two thetas in the slab: T1 at 0, Phi1 at

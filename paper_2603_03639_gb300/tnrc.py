@@ -22,7 +22,8 @@ EXPORTS = ("tnrc_create", "tnrc_set_controls", "tnrc_sample_noise", "tnrc_set_no
            "tnrc_fidelity_grad", "tnrc_get_overlaps", "tnrc_get_stats", "tnrc_set_controls_dev",
            "tnrc_evaluate_dev", "tnrc_sync", "tnrc_footprint", "tnrc_destroy", "tnrc_status_string",
            "tnrc_fidelity_static", "tnrc_set_graphs", "tnrc_last_error", "tnrc_measure_fp64_peak",
-           "tnrc_measure_dmma_peak", "tnrc_set_pooled", "tnrc_set_stream", "tnrc_fidelity_grad_plain")
+           "tnrc_measure_dmma_peak", "tnrc_set_pooled", "tnrc_set_stream", "tnrc_fidelity_grad_plain",
+           "tnrc_set_svd_shape")
 
 
 class TNRCError(RuntimeError):
@@ -99,6 +100,8 @@ def lib() -> ctypes.CDLL:
         L.tnrc_set_stream.restype = i32
         L.tnrc_fidelity_grad_plain.argtypes = [vp, dp, dp]
         L.tnrc_fidelity_grad_plain.restype = i32
+        L.tnrc_set_svd_shape.argtypes = [vp, i32]
+        L.tnrc_set_svd_shape.restype = i32
         L.tnrc_footprint.argtypes = [ctypes.POINTER(Problem)]
         L.tnrc_footprint.restype = ctypes.c_size_t
         L.tnrc_destroy.argtypes = [vp]
@@ -324,6 +327,10 @@ class Context:
         """Order later work on another CUDA stream (waits for queued work)."""
         _check(lib().tnrc_set_stream(self._h, ctypes.c_void_p(stream or None)), "tnrc_set_stream", self._h)
         self.stream = int(stream or 0)
+
+    def set_svd_shape(self, pairs: bool = True):
+        """Two small SVDs per warp on the half-warps (True) or one per warp."""
+        _check(lib().tnrc_set_svd_shape(self._h, 1 if pairs else 0), "tnrc_set_svd_shape", self._h)
 
     def set_pooled(self, enable: bool = True):
         """One CTA per trajectory with work regions from a pool (see the header)."""

@@ -395,3 +395,24 @@ def test_plain_path_equals_batched_launch(name):
     Fo, go, _ = robust.ensemble(oracle_problem(w, u, mask, J, ins, tgs))
     assert abs(Fp - Fo) <= TOL_F
     assert grad_close(gp, go)
+
+
+@pytest.mark.parametrize("shape", [(8, 1), (4, 2)])
+def test_svd_shape_pairs_and_one_per_warp(shape):
+    """Both matrix shapes -- two small SVDs per warp on the half-warps, and one
+    SVD per warp -- meet the oracle's bars, forward and costate, on a case
+    whose bonds are small enough to pair and one with wider thetas."""
+    for w in (synth.WORKLOADS["cnot50"].replace(N=12, K=6, chi=16, M=3, P=2),
+              synth.WORKLOADS["ghz30"].replace(N=12, K=5, chi=32, M=1, P=1, u_sigma=1.5, dt=0.25)):
+        u, mask, J, ins, tgs = case(w)
+        Fo, go, Oo = robust.ensemble(oracle_problem(w, u, mask, J, ins, tgs))
+        for pairs in (True, False):
+            ctx = gpu_context(w, ins, tgs, mask, warps=shape[0], ctas_per_sm=shape[1])
+            ctx.set_svd_shape(pairs)
+            ctx.set_controls(u)
+            ctx.set_noise(J)
+            F, g = ctx.fidelity_grad()
+            assert abs(F - Fo) <= TOL_F
+            assert np.max(np.abs(ctx.overlaps() - Oo)) <= TOL_O
+            assert grad_close(g, go)
+            ctx.close()
