@@ -8,8 +8,8 @@ own noise seed.  The server
     gate tables, MPS and costate working slots) and reuses them for every
     later request of their problem, as an optimiser's iterations do; a
     request for a problem whose resident contexts are all busy gets another
-    resident copy (made once, then reused like the first), so one problem
-    can have several requests in flight;
+    resident copy (made once, then reused like the first; at most max_copies
+    per problem), so one problem can have several requests in flight;
   * admits a request when its context's device footprint fits the memory
     budget next to the contexts already holding work (idle contexts are
     destroyed first, least recently used, when memory is short);
@@ -160,10 +160,13 @@ class Server:
     short_s: a request whose problem has been served in at most this many
     seconds of device time runs on a high-priority stream, so that its CTAs
     start before the pending CTAs of longer requests (shortest work first at
-    trajectory granularity); a problem not yet measured runs at low priority."""
+    trajectory granularity); a problem not yet measured runs at low priority;
+    max_copies: resident contexts one problem may have, so that that many of
+    its requests can be in flight at once (further ones wait for a copy to
+    come free rather than for a new context to be built)."""
 
     def __init__(self, mem_budget: Optional[int] = None, max_inflight: int = 8, device: int = 0,
-                 short_s: float = 0.1):
+                 short_s: float = 0.1, max_copies: int = 2):
         import torch
         self.device = torch.device("cuda", device)
         if mem_budget is None:
@@ -172,6 +175,7 @@ class Server:
         self.mem_budget = mem_budget
         self.max_inflight = max_inflight
         self.short_s = short_s
+        self.max_copies = max_copies
         self.key_service: dict = {}
         self.pending = collections.deque()
         self.slots: list = []
@@ -238,12 +242,21 @@ class Server:
             self.key_service[key] = min(known + ([self.key_service[key]] if key in self.key_service else []))
         return self.key_service.get(key)
 
-    def _next_pending(self) -> Request:
-        """The pending request to admit next: the one whose problem has the
+    def _admissible(self, req: Request) -> bool:
+        """A resident copy of the request's problem is idle, or another copy
+        may be made (at most max_copies per problem)."""
+        mine = [s for s in self.slots if s.key == req.key]
+        return any(s.busy is None for s in mine) or len(mine) < self.max_copies
+
+    def _next_pending(self) -> Optional[Request]:
+        """The pending request to admit next: among those whose problem has an
+        idle resident copy (or may get one), the one whose problem has the
         shortest measured service time; unmeasured problems after measured
         ones; arrival order among equals."""
         best, best_t = None, None
         for r in self.pending:
+            if not self._admissible(r):
+                continue
             t = self._service(r.key)
             t = float("inf") if t is None else t
             if best is None or t < best_t:
@@ -308,6 +321,8 @@ class Server:
                 inflight = sum(1 for s in self.slots if s.busy is not None)
                 while self.pending:
                     req = self._next_pending()
+                    if req is None:
+                        break
                     t = self._service(req.key)
                     short = t is not None and t <= self.short_s
                     # a short request is admitted past the in-flight cap (up to
