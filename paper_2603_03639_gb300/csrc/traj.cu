@@ -397,19 +397,31 @@ __device__ void pack_state(const TrajParams& p, const Lay& Y, const unsigned cha
 // Transfer-matrix steps of <c| . |a>.
 // Left:  Eout[b'][a'] = sum_{b,s,a} conj(c[b][s][b']) Ein[b][a] a[a][s][a']
 // Right: Eout[b][a]   = sum_{s,b',a'} conj(c[b][s][b']) Ein[b'][a'] a[a][s][a']
+// Run by a team of nt threads (thread ti of the team): one warp (nt = 32,
+// bar < 0: the warp synchronises itself) or several warps meeting at the
+// named barrier `bar`.  Every output element is summed by one thread in the
+// same order whatever the team, so the result does not depend on it.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void team_sync(int bar, int nt) {
+  if (bar < 0)
+    __syncwarp();
+  else
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
+}
+
 template <int kD>
 __device__ void env_left_step(const double2* Ein, int Dcl, int Dal, const double2* c, int Dcr,
-                              const double2* a, int Dar, double2* tmp, double2* Eout, int lane) {
+                              const double2* a, int Dar, double2* tmp, double2* Eout, int ti, int nt = 32,
+                              int bar = -1) {
   const int w2 = kD * Dar;
-  for (int it = lane; it < Dcl * w2; it += 32) {
+  for (int it = ti; it < Dcl * w2; it += nt) {
     const int be = it / w2, rest = it - be * w2;
     double2 acc = make_double2(0.0, 0.0);
     for (int al = 0; al < Dal; ++al) cfma(acc, Ein[be * Dal + al], a[(size_t)al * w2 + rest]);
     tmp[it] = acc;
   }
-  __syncwarp();
-  for (int it = lane; it < Dcr * Dar; it += 32) {
+  team_sync(bar, nt);
+  for (int it = ti; it < Dcr * Dar; it += nt) {
     const int bp = it / Dar, ap = it - bp * Dar;
     double2 acc = make_double2(0.0, 0.0);
     for (int be = 0; be < Dcl; ++be)
@@ -418,22 +430,23 @@ __device__ void env_left_step(const double2* Ein, int Dcl, int Dal, const double
         cfmac(acc, c[(size_t)be * kD * Dcr + s * Dcr + bp], tmp[(size_t)be * w2 + s * Dar + ap]);
     Eout[it] = acc;
   }
-  __syncwarp();
+  team_sync(bar, nt);
 }
 
 template <int kD>
 __device__ void env_right_step(const double2* Ein, int Dcr, int Dar, const double2* c, int Dcl,
-                               const double2* a, int Dal, double2* tmp, double2* Eout, int lane) {
+                               const double2* a, int Dal, double2* tmp, double2* Eout, int ti, int nt = 32,
+                               int bar = -1) {
   const int w2 = kD * Dal;
-  for (int it = lane; it < Dcr * w2; it += 32) {
+  for (int it = ti; it < Dcr * w2; it += nt) {
     const int bp = it / w2, rest = it - bp * w2;
     const int s = rest / Dal, al = rest - s * Dal;
     double2 acc = make_double2(0.0, 0.0);
     for (int ap = 0; ap < Dar; ++ap) cfma(acc, Ein[bp * Dar + ap], a[(size_t)al * kD * Dar + s * Dar + ap]);
     tmp[it] = acc;
   }
-  __syncwarp();
-  for (int it = lane; it < Dcl * Dal; it += 32) {
+  team_sync(bar, nt);
+  for (int it = ti; it < Dcl * Dal; it += nt) {
     const int be = it / Dal, al = it - be * Dal;
     double2 acc = make_double2(0.0, 0.0);
     for (int bp = 0; bp < Dcr; ++bp)
@@ -442,7 +455,7 @@ __device__ void env_right_step(const double2* Ein, int Dcr, int Dar, const doubl
         cfmac(acc, c[(size_t)be * kD * Dcr + s * Dcr + bp], tmp[(size_t)bp * w2 + s * Dal + al]);
     Eout[it] = acc;
   }
-  __syncwarp();
+  team_sync(bar, nt);
 }
 
 // <t|a> by one warp.
@@ -520,22 +533,31 @@ __device__ void layer_envs(const TrajParams& p, const Lay& Y, const unsigned cha
   double2* Rbuf = Lbuf + (size_t)(N + 1) * cc;
   const int lane = w.lane;
 
-  // left environments L_i (sites < i) for i <= N-2, right R_i (sites >= i) for i >= 2
+  // left environments L_i (sites < i) for i <= N-2 by the even warps, right
+  // R_i (sites >= i) for i >= 2 by the odd warps: each sweep is sequential
+  // over the sites, so each step is shared by its team of warps (named
+  // barriers 1 and 2); the step's intermediate (at most Dc x kD Da) sits in
+  // the team's first warp's shared slab when it fits, else in its scratch
   TNRC_TIC(t_e);
-  if (warp == 0) {
+  const int team = warp & 1;                               // 0: left, 1: right
+  const int nt = 32 * (team == 0 ? (p.warps + 1) / 2 : p.warps / 2);
+  const int ti = (warp >> 1) * 32 + lane;
+  double2* lead_slab = w.slab - (size_t)(warp - team) * p.slab_elems;
+  double2* lead_scratch = w.scratch - (size_t)(warp - team) * p.scratch_elems;
+  const bool lead = warp == team;
+  if (team == 0) {
     for (int i = 0; i + 1 <= N - 2; ++i) {
-      // the step's intermediate (Dc[i] x kD Da[i+1]) in the warp's shared slab when it fits
-      double2* tmp = (Dc[i] * kD * Da[i + 1] <= p.slab_elems) ? w.slab : w.scratch;
+      double2* tmp = (Dc[i] * kD * Da[i + 1] <= p.slab_elems) ? lead_slab : lead_scratch;
       env_left_step<kD>(Lbuf + i * cc, Dc[i], Da[i], cs + so[i], Dc[i + 1], as + ao[i], Da[i + 1],
-                        tmp, Lbuf + (i + 1) * cc, lane);
-      w.alg += 8ull * kD * Da[i + 1] * (unsigned long long)(Dc[i] * Da[i] + Dc[i + 1] * Dc[i]);
+                        tmp, Lbuf + (i + 1) * cc, ti, nt, 1);
+      if (lead) w.alg += 8ull * kD * Da[i + 1] * (unsigned long long)(Dc[i] * Da[i] + Dc[i + 1] * Dc[i]);
     }
-  } else if (warp == 1) {
+  } else {
     for (int i = N - 1; i >= 2; --i) {
-      double2* tmp = (Dc[i + 1] * kD * Da[i] <= p.slab_elems) ? w.slab : w.scratch;
+      double2* tmp = (Dc[i + 1] * kD * Da[i] <= p.slab_elems) ? lead_slab : lead_scratch;
       env_right_step<kD>(Rbuf + (size_t)(i + 1) * cc, Dc[i + 1], Da[i + 1], cs + so[i], Dc[i],
-                         as + ao[i], Da[i], tmp, Rbuf + (size_t)i * cc, lane);
-      w.alg += 8ull * kD * Da[i] * (unsigned long long)(Dc[i + 1] * Da[i + 1] + Dc[i] * Dc[i + 1]);
+                         as + ao[i], Da[i], tmp, Rbuf + (size_t)i * cc, ti, nt, 2);
+      if (lead) w.alg += 8ull * kD * Da[i] * (unsigned long long)(Dc[i + 1] * Da[i + 1] + Dc[i] * Dc[i + 1]);
     }
   }
   TNRC_TOC(w, 4, t_e);
