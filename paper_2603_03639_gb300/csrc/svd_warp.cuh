@@ -50,6 +50,59 @@ __device__ __forceinline__ unsigned group_mask(int g, int gb) {
   return (g >= 32) ? 0xffffffffu : (((1u << g) - 1u) << gb);
 }
 
+// FP64 warp instructions of a unit loop that gives g lanes to each of
+// `units` units (the trailing columns of a QR step, the pairs of a Jacobi
+// round) of `rows` rows on `lanes` lanes: iterations x (rows per lane x
+// per_row + fixed + per_level x reduction levels).
+__device__ __forceinline__ int unit_loop_cost(int units, int rows, int g, int lanes, int per_row, int fixed,
+                                              int per_level) {
+  const int gpw = lanes / g;
+  const int iters = (units + gpw - 1) / gpw;
+  int lv = 0;
+  while ((1 << lv) < g) ++lv;
+  return iters * (((rows + g - 1) / g) * per_row + fixed + per_level * lv);
+}
+
+// Lanes per unit.  With units <= lanes / 2 every unit gets floor(lanes /
+// units) lanes in one iteration.  Beyond that one lane per unit leaves lanes
+// idle (or takes a second, partly idle iteration), and groups of 2..8 lanes
+// over more iterations can cost fewer FP64 warp instructions -- 41 columns
+// of 80 rows: 2 iterations of 80 rows on single lanes, or 6 of 20 rows on
+// groups of 4 -- so the cheapest by unit_loop_cost is taken when it beats one
+// lane per unit by more than 1/16.  The choice depends only on the sizes.
+__device__ __forceinline__ int pick_lanes(int units, int rows, int lanes, int per_row, int fixed, int per_level) {
+  if (units < 1) return lanes;
+  if (2 * units <= lanes) return lanes / units;
+  int best = 1;
+  int bc = unit_loop_cost(units, rows, 1, lanes, per_row, fixed, per_level);
+  const int c1 = bc;
+  for (int g = 2; g <= 8; ++g) {
+    const int c = unit_loop_cost(units, rows, g, lanes, per_row, fixed, per_level);
+    if (c < bc && 16 * c < 15 * c1) {
+      bc = c;
+      best = g;
+    }
+  }
+  return best;
+}
+
+// Per-unit FP64 instruction counts of the two loops (rows: per row of the
+// unit; fixed: scalars per unit; level: per level of the group reduction).
+constexpr int kQrRow = 11, kQrFixed = 2, kQrLevel = 3;      // QR step: <v, x>, x -= v s, |x|^2
+constexpr int kJacRow = 16, kJacFixed = 40, kJacLevel = 2;  // Jacobi round: <a, b>, rotation
+
+// Lanes per unit: one iteration with floor(lanes / units) lanes each (one
+// lane per unit from `lanes` units on), or, with kModel, the pick_lanes
+// choice.  The qubit-state kernels keep the first (their theta are at most
+// 32 rows on the benchmark, where the model's choices measured slower); the
+// operator kernels, whose theta are 40 to 80 rows wide, take the model.
+template <bool kModel>
+__device__ __forceinline__ int lanes_per_unit(int units, int rows, int lanes, int per_row, int fixed,
+                                              int per_level) {
+  if (kModel) return pick_lanes(units, rows, lanes, per_row, fixed, per_level);
+  return units >= lanes ? 1 : lanes / units;
+}
+
 // out[c] = |column c|^2 for the m columns of length n of T (column-major),
 // with g = 32 / m lanes per column (any g), so that short columns keep most
 // lanes busy.
@@ -76,8 +129,9 @@ __device__ inline void warp_col_norms(const double2* T, int n, int m, double* ou
 // Lanes per pair: an odd m is padded with a zero column, which the circle
 // ordering pairs with a different real column in every round (pair q = 0);
 // that pair needs no work, so the Pe = floor(m / 2) real pairs of a round
-// share the 32 lanes, g = floor(32 / Pe) each (not necessarily a power of
-// two).  Each lane then owns ceil(n / g) rows of its pair.
+// share the 32 lanes, g = lanes_per_unit(Pe, n) each (floor(32 / Pe), or
+// the instruction-count choice with kModel; not necessarily a power of two).
+// Each lane then owns ceil(n / g) rows of its pair.
 //
 // The norms are computed exactly before the first sweep and in the first
 // round of every sweep (where the pair's lanes form all three inner
@@ -85,6 +139,7 @@ __device__ inline void warp_col_norms(const double2* T, int n, int m, double* ou
 // carried through each rotation by |a'|^2 = |a|^2 - t |<a,b>|,
 // |b'|^2 = |b|^2 + t |<a,b>| (t = tan theta), recomputed from the rotated
 // column should a norm fall below 1/16 of its old value (cancellation).
+template <bool kModel = false>
 __device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, double* cn, int lane) {
   const int mp = m + (m & 1);
   if (mp < 2 || n < 1) return 0;
@@ -92,7 +147,7 @@ __device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, double*
   const int q0 = m & 1;          // pair 0 holds the padding column of an odd m
   const int Pe = P - q0;         // real pairs per round
   if (Pe < 1) return 1;          // a single column is already orthogonal
-  const int g = Pe >= 32 ? 1 : 32 / Pe;
+  const int g = lanes_per_unit<kModel>(Pe, n, 32, kJacRow, kJacFixed, kJacLevel);
   const int groups = 32 / g;
   const int gi = lane / g, lig = lane - gi * g, gb = gi * g;
   const unsigned gmask = group_mask(g, gb);
@@ -207,7 +262,8 @@ __device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, double*
 // Step j takes the remaining column of largest norm as pivot; when that norm
 // squared is <= thr, every remaining column is below it and the
 // factorisation stops with r = j.  The trailing columns of a step are shared
-// out to groups of G = floor(32 / columns) lanes, each group's lanes
+// out to groups of G = lanes_per_unit(columns, rows) lanes (floor(32 /
+// columns), or the instruction-count choice with kModel), each group's lanes
 // splitting the rows; the trailing column norms are recomputed exactly while
 // the reflector is applied,
 // so the pivot choice needs no norm downdating.  Reductions within a group
@@ -218,6 +274,7 @@ __device__ inline int warp_jacobi(double2* T, int n, int m, double fro2, double*
 // On return rows 0..r-1 of W hold R (zeros below the diagonal; row j is the
 // j-th row of R in the pivoted column order), piv[c] is the original index of
 // pivoted column c (c < n), and qn (n doubles) has been used as scratch.
+template <bool kModel = false>
 __device__ inline int warp_qrcp(double2* W, int m, int n, double thr, int* piv, double* qn, int lane) {
   {
     const int G = n >= 32 ? 1 : 32 / n;
@@ -280,11 +337,12 @@ __device__ inline int warp_qrcp(double2* W, int m, int n, double thr, int* piv, 
     const double2 ph = (ax0 > 0.0) ? cscale(x0, 1.0 / ax0) : make_double2(1.0, 0.0);
     const double2 v0 = cscale(ph, ax0 + xn);
     const double beta = 1.0 / (xn * (xn + ax0));
-    // the na = n - j - 1 trailing columns share the 32 lanes, G = 32 / na
-    // lanes each (any G), so that the lanes stay busy as the columns run out
+    // the na = n - j - 1 trailing columns share the 32 lanes, G =
+    // lanes_per_unit(na, m - j) lanes each (any G), so that the lanes stay busy
+    // as the columns run out
     const int na = n - j - 1;
     if (na > 0) {
-      const int G = na >= 32 ? 1 : 32 / na;
+      const int G = lanes_per_unit<kModel>(na, m - j, 32, kQrRow, kQrFixed, kQrLevel);
       const int groups = 32 / G;
       const int gi = lane / G, lig = lane - gi * G, gb = gi * G;
       const unsigned gmask = group_mask(G, gb);
@@ -322,6 +380,120 @@ __device__ inline int warp_qrcp(double2* W, int m, int n, double thr, int* piv, 
   return steps;
 }
 
+// The second QR of the Drmac-Veselic preconditioner, taken here to shorten
+// the columns the Jacobi works on.  X = R^dagger (n x r, column-major, column
+// j at X + j n) is factorised X = Q2 R2 by Householder reflections without
+// pivoting; R2 (r x r, upper triangular) is written column-major to R2 with
+// zeros below the diagonal, and Q2 (n x r, orthonormal columns) overwrites X.
+// X and R2 have the same Gram matrix (X^dag X = R2^dag R2), so one-sided
+// Jacobi on the r columns of R2 makes the same rotations as on X, on columns
+// of length r instead of n: R2 V = Z2 S gives X V = (Q2 Z2) S.  vh (r
+// complex) and beta (r doubles) are shared scratch.
+template <bool kModel>
+static __device__ __noinline__ void warp_qr_rows(double2* X, int n, int r, double2* R2, double2* vh, double* beta,
+                                                int lane) {
+  for (int j = 0; j < r; ++j) {
+    double2* xj = X + (size_t)j * n;
+    double s = 0.0;
+    for (int i = j + lane; i < n; i += 32) s += cabs2(xj[i]);
+    const double xn2 = warp_sum(s);
+    // reflector H_j = I - beta v v^dag mapping rows j..n-1 of column j to
+    // alpha e_j: alpha = -e^{i arg x0} |x|, v = x - alpha e_j
+    const double2 x0 = xj[j];
+    const double xn = sqrt(xn2);
+    const double ax0 = sqrt(cabs2(x0));
+    const double2 ph = (ax0 > 0.0) ? cscale(x0, 1.0 / ax0) : make_double2(1.0, 0.0);
+    const double2 v0 = cscale(ph, ax0 + xn);
+    const double bt = (xn > 0.0) ? 1.0 / (xn * (xn + ax0)) : 0.0;
+    const int na = r - j - 1;
+    if (na > 0) {
+      const int G = lanes_per_unit<kModel>(na, n - j, 32, kQrRow - 3, kQrFixed, 2);
+      const int groups = 32 / G;
+      const int gi = lane / G, lig = lane - gi * G, gb = gi * G;
+      const unsigned gmask = group_mask(G, gb);
+      for (int c = j + 1 + gi; c < r && gi < groups; c += groups) {
+        double2* xc = X + (size_t)c * n;
+        double2 sc = make_double2(0.0, 0.0);
+        for (int i = j + lig; i < n; i += G) cfmac(sc, (i == j) ? v0 : xj[i], xc[i]);
+        if (G > 1) {
+          sc.x = group_sum(sc.x, G, lig, gb, gmask);
+          sc.y = group_sum(sc.y, G, lig, gb, gmask);
+        }
+        sc = cscale(sc, bt);
+        for (int i = j + lig; i < n; i += G) {
+          const double2 vi = (i == j) ? v0 : xj[i];
+          double2 x = xc[i];
+          x.x = fma(-vi.x, sc.x, x.x);
+          x.x = fma(vi.y, sc.y, x.x);
+          x.y = fma(-vi.x, sc.y, x.y);
+          x.y = fma(-vi.y, sc.x, x.y);
+          xc[i] = x;
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      vh[j] = v0;
+      beta[j] = bt;
+      xj[j] = make_double2(-xn * ph.x, -xn * ph.y);   // R2[j][j]; rows below keep v's tail
+    }
+    __syncwarp();
+  }
+  for (int e = lane; e < r * r; e += 32) {
+    const int c = e / r, i = e - c * r;
+    R2[e] = (i <= c) ? X[(size_t)c * n + i] : make_double2(0.0, 0.0);
+  }
+  __syncwarp();
+  // Q2 = H_0 H_1 ... H_{r-1} [I_r; 0] in place, from the last reflector back:
+  // before step j, column c > j holds H_{j+1} .. H_{r-1} e_c (zero above row
+  // j+1) and column j still holds v's tail; step j applies H_j to the columns
+  // c > j, then writes H_j e_j over column j.
+  for (int j = r - 1; j >= 0; --j) {
+    double2* xj = X + (size_t)j * n;
+    const double2 v0 = vh[j];
+    const double bt = beta[j];
+    const int na = r - j - 1;
+    if (na > 0) {
+      const int G = lanes_per_unit<kModel>(na, n - j, 32, kQrRow - 3, kQrFixed, 2);
+      const int groups = 32 / G;
+      const int gi = lane / G, lig = lane - gi * G, gb = gi * G;
+      const unsigned gmask = group_mask(G, gb);
+      for (int c = j + 1 + gi; c < r && gi < groups; c += groups) {
+        double2* xc = X + (size_t)c * n;
+        double2 sc = make_double2(0.0, 0.0);
+        for (int i = j + lig; i < n; i += G) cfmac(sc, (i == j) ? v0 : xj[i], xc[i]);
+        if (G > 1) {
+          sc.x = group_sum(sc.x, G, lig, gb, gmask);
+          sc.y = group_sum(sc.y, G, lig, gb, gmask);
+        }
+        sc = cscale(sc, bt);
+        for (int i = j + lig; i < n; i += G) {
+          const double2 vi = (i == j) ? v0 : xj[i];
+          double2 x = xc[i];
+          x.x = fma(-vi.x, sc.x, x.x);
+          x.x = fma(vi.y, sc.y, x.x);
+          x.y = fma(-vi.x, sc.y, x.y);
+          x.y = fma(-vi.y, sc.x, x.y);
+          xc[i] = x;
+        }
+      }
+    }
+    __syncwarp();
+    // H_j e_j = e_j - beta v conj(v_j): zero above row j
+    for (int i = lane; i < n; i += 32) {
+      double2 q = make_double2(0.0, 0.0);
+      if (i == j) {
+        q = make_double2(1.0 - bt * cabs2(v0), 0.0);
+      } else if (i > j) {
+        const double2 vi = xj[i];
+        q = make_double2(-bt * (vi.x * v0.x + vi.y * v0.y), -bt * (vi.y * v0.x - vi.x * v0.y));
+      }
+      xj[i] = q;
+    }
+    __syncwarp();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Two matrices per warp.  For small matrices a Jacobi round costs mostly its
 // per-pair scalars (inner products reduced, two reciprocal square roots, the
@@ -350,6 +522,7 @@ __device__ inline void half_col_norms(const double2* T, int n, int m, double* ou
 
 // warp_qrcp on each half's matrix (W m x n row-major, thr, piv, qn its own);
 // returns this half's numerical rank.
+template <bool kModel = false>
 __device__ inline int half_qrcp(double2* W, int m, int n, double thr, int* piv, double* qn, int lane) {
   const int hb = lane & 16, ll = lane & 15;
   const unsigned hmask = 0xffffu << hb;
@@ -426,7 +599,7 @@ __device__ inline int half_qrcp(double2* W, int m, int n, double thr, int* piv, 
       const double beta = 1.0 / (xn * (xn + ax0));
       const int na = n - j - 1;
       if (na > 0) {
-        const int G = na >= 16 ? 1 : 16 / na;
+        const int G = lanes_per_unit<kModel>(na, m - j, 16, kQrRow, kQrFixed, kQrLevel);
         const int groups = 16 / G;
         const int gi = ll / G, lig = ll - gi * G, gb = hb + gi * G;
         const unsigned gmask = group_mask(G, gb);
@@ -469,6 +642,7 @@ __device__ inline int half_qrcp(double2* W, int m, int n, double thr, int* piv, 
 
 // warp_jacobi on each half's matrix (T n x m column-major, fro2, cn its own);
 // returns this half's sweep count (or -kMaxSweeps).
+template <bool kModel = false>
 __device__ inline int half_jacobi(double2* T, int n, int m, double fro2, double* cn, int lane) {
   const int hb = lane & 16, ll = lane & 15;
   const unsigned hmask = 0xffffu << hb;
@@ -477,7 +651,7 @@ __device__ inline int half_jacobi(double2* T, int n, int m, double fro2, double*
   const int q0 = m & 1;
   const int Pe = P - q0;
   const bool trivial = (mp < 2 || n < 1 || Pe < 1);
-  const int g = (trivial || Pe >= 16) ? 1 : 16 / Pe;
+  const int g = trivial ? 1 : lanes_per_unit<kModel>(Pe, n, 16, kJacRow, kJacFixed, kJacLevel);
   const int groups = 16 / g;
   const int gi = ll / g, lig = ll - gi * g, gb = hb + gi * g;
   const unsigned gmask = group_mask(g, gb);

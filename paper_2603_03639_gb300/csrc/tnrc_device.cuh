@@ -22,6 +22,7 @@ constexpr double kZeroFloor = 1e-13;        // relative numerical-zero level of 
 constexpr double kJacobiZero = 5e-15;       // columns below this x ||theta||_F are left alone
 constexpr double kJacobiQuad = 1e-20;       // |<a,b>|^2 / (|a|^2 |b|^2) of a rotation that counts as
                                             // large: a sweep with none is the last (quadratic convergence)
+constexpr int kRowQrMinRank = 8;            // second QR of R^dagger from this rank on, when n >= 2.5 r
 
 // device status bits (OR-ed into *status)
 constexpr int kStatusNoConverge = 1;

@@ -170,13 +170,43 @@ __device__ double theta_build(const TrajParams& p, const Lay& Y, unsigned char* 
   return fro;
 }
 
+// The split after the second QR: Z = Q2 Z2 (T holds Q2, n x r; Z2 the
+// rotated columns of R2, r x r) formed while B_{b+1} = Y_k^dag is written,
+// then B_b = Phi Y_k / |S_k| from B_{b+1} (Y[piv[c]][i] = conj(B_{b+1}[i][
+// piv[c]])).  Out of line: the common path of theta_finish stays as it is.
+static __device__ __noinline__ void split_q2(const double2* T, const double2* Z2, const double2* Phi, double2* Bt,
+                                      double2* A, const int* perm, const int* piv, const double* isig, int m,
+                                      int n, int r, int k, double inv_kn, int lane) {
+  for (int it = lane; it < k * n; it += 32) {
+    const int i = it / n, c = it - i * n;
+    const double2* z2 = Z2 + (size_t)perm[i] * r;
+    double2 z = make_double2(0.0, 0.0);
+    for (int l = 0; l < r; ++l) cfma(z, T[(size_t)l * n + c], z2[l]);
+    Bt[(size_t)i * n + piv[c]] = cscale(cconj(z), isig[i]);
+  }
+  __syncwarp();
+  for (int it = lane; it < m * k; it += 32) {
+    const int row = it / k, i = it - row * k;
+    const double2* ph = Phi + (size_t)row * n;
+    const double2* bt = Bt + (size_t)i * n;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int c = 0; c < n; ++c) cfmac(acc, bt[c], ph[c]);
+    A[it] = cscale(acc, inv_kn);
+  }
+  __syncwarp();
+}
+
 // Phases 3 and 4 of a two-site update of bond b, after the SVD left R^dagger
 // V = Z S in T (r columns of length n; QR pivots in bf.piv): rank and
 // truncate, then lam_b <- S_k / |S_k|, B_{b+1} <- Y_k^dag, B_b <- Phi Y_k /
-// |S_k|, where Y[piv[c]][i] = Z[c][i] = T[perm[i] n + c] / sigma_i.
+// |S_k|, where Y[piv[c]][i] = Z[c][i] = T[perm[i] n + c] / sigma_i.  After
+// the second QR (Z2 given) T holds Q2 (n x r) and Z2 (r x r) the rotated
+// columns of R2, so that Z[c][i] = sum_l T[l n + c] Z2[perm[i] r + l] /
+// sigma_i.
 template <int kD>
 __device__ void theta_finish(const TrajParams& p, const Lay& Y, unsigned char* slot, int b, double2* T,
-                             const double2* Phi, int r, int sw, bool record, bool count, WarpCtx& w, SvdBufs bf) {
+                             const double2* Phi, int r, int sw, bool record, bool count, WarpCtx& w, SvdBufs bf,
+                             const double2* Z2 = nullptr) {
   const int lane = w.lane;
   const int lstride = Y.L.chi;
   int* D = slot_dims(slot);
@@ -189,7 +219,7 @@ __device__ void theta_finish(const TrajParams& p, const Lay& Y, unsigned char* s
 
   TNRC_TIC(t_r);
   double kept2, tot2, gap;
-  int k = warp_rank_truncate(T, n, r, p.chi, p.eps, bf.sig2, bf.perm, lane, kept2, tot2, gap);
+  int k = warp_rank_truncate(Z2 ? Z2 : T, Z2 ? r : n, r, p.chi, p.eps, bf.sig2, bf.perm, lane, kept2, tot2, gap);
   if (k > Y.dcap[b + 1]) {  // cannot happen (k <= min(m, n, chi)); keeps memory in bounds regardless
     k = Y.dcap[b + 1];
     if (lane == 0) atomicOr(p.status, kStatusBadDims);
@@ -225,6 +255,13 @@ __device__ void theta_finish(const TrajParams& p, const Lay& Y, unsigned char* s
     isig[i] = rsqrt(bf.sig2[bf.perm[i]]);
   }
   __syncwarp();
+  if (Z2) {
+    split_q2(T, Z2, Phi, Bt, A, bf.perm, piv, isig, m, n, r, k, inv_kn, lane);
+    if (lane == 0) D[b + 1] = k;
+    __syncwarp();
+    TNRC_TOC(w, 3, t_w);
+    return;
+  }
   for (int it = lane; it < k * n; it += 32) {
     const int i = it / n, c = it - i * n;
     const int j = bf.perm[i];
@@ -262,15 +299,24 @@ __device__ void two_site_update(const TrajParams& p, const Lay& Y, unsigned char
   // R^dagger (column j = conjugated row j of R, contiguous at T + j n).
   TNRC_TIC(t_j);
   const double zthr = kJacobiZero * kJacobiZero * fro;
-  int r = warp_qrcp(T, m, n, zthr, w.piv, w.qn, lane);
+  int r = warp_qrcp<kD == 4>(T, m, n, zthr, w.piv, w.qn, lane);
   if (r < 1) r = 1;  // theta == 0 (or not finite): keep one column; the NaN check reports it
   for (int e = lane; e < r * n; e += 32) T[e] = cconj(T[e]);
   __syncwarp();
+  // columns of R^dagger much longer than their number: the second QR, after
+  // which the Jacobi runs on r x r (Z2 in theta's home past R^dagger when it
+  // fits there, else in the warp's scratch past theta's room)
+  double2* Z2 = nullptr;
+  if (r >= kRowQrMinRank && 2 * n >= 5 * r) {
+    Z2 = (T == w.slab && (size_t)(m - r) * n >= (size_t)r * r) ? T + (size_t)r * n
+                                                              : w.scratch + (size_t)2 * kD * kD * p.chi * p.chi;
+    warp_qr_rows<kD == 4>(T, n, r, Z2, w.small, w.sig2, lane);
+  }
   TNRC_TOC(w, 1, t_j);
   TNRC_TIC(t_s);
-  const int sw = warp_jacobi(T, n, r, fro, w.qn, lane);   // qn is free after the QR
+  const int sw = warp_jacobi<kD == 4>(Z2 ? Z2 : T, Z2 ? r : n, r, fro, w.qn, lane);   // qn is free after the QR
   TNRC_TOC(w, 8, t_s);
-  theta_finish<kD>(p, Y, slot, b, T, Phi, r, sw, record, count, w, SvdBufs{w.sig2, w.qn, w.perm, w.piv});
+  theta_finish<kD>(p, Y, slot, b, T, Phi, r, sw, record, count, w, SvdBufs{w.sig2, w.qn, w.perm, w.piv}, Z2);
 }
 
 // Whether bonds b1 and b2 of one layer are updated as a pair: pairing is on
@@ -317,9 +363,9 @@ __device__ void two_site_update_pair(const TrajParams& p, const Lay& Y, unsigned
   const SvdBufs bf2{w.sig2 + 64, w.qn + 64, w.perm + 64, w.piv + 64};
   const bool hi = lane >= 16;
   TNRC_TIC(t_j);
-  int rh = half_qrcp(hi ? T2 : T1, hi ? m2 : m1, hi ? n2 : n1,
-                     kJacobiZero * kJacobiZero * (hi ? fro2 : fro1), hi ? bf2.piv : bf1.piv,
-                     hi ? bf2.qn : bf1.qn, lane);
+  int rh = half_qrcp<kD == 4>(hi ? T2 : T1, hi ? m2 : m1, hi ? n2 : n1,
+                              kJacobiZero * kJacobiZero * (hi ? fro2 : fro1), hi ? bf2.piv : bf1.piv,
+                              hi ? bf2.qn : bf1.qn, lane);
   int r1 = __shfl_sync(0xffffffffu, rh, 0), r2 = __shfl_sync(0xffffffffu, rh, 16);
   if (r1 < 1) r1 = 1;
   if (r2 < 1) r2 = 1;
@@ -328,8 +374,8 @@ __device__ void two_site_update_pair(const TrajParams& p, const Lay& Y, unsigned
   __syncwarp();
   TNRC_TOC(w, 1, t_j);
   TNRC_TIC(t_s);
-  const int swh = half_jacobi(hi ? T2 : T1, hi ? n2 : n1, hi ? r2 : r1, hi ? fro2 : fro1, hi ? bf2.qn : bf1.qn,
-                              lane);
+  const int swh = half_jacobi<kD == 4>(hi ? T2 : T1, hi ? n2 : n1, hi ? r2 : r1, hi ? fro2 : fro1,
+                                       hi ? bf2.qn : bf1.qn, lane);
   const int sw1 = __shfl_sync(0xffffffffu, swh, 0), sw2 = __shfl_sync(0xffffffffu, swh, 16);
   TNRC_TOC(w, 8, t_s);
   theta_finish<kD>(p, Y, slot, b1, T1, Phi1, r1, sw1, record, count, w, bf1);
