@@ -134,10 +134,10 @@ typedef struct {
                                     did not fit their CTA's region packed and that were redone
                                     with checkpoints (results are identical either way)     */
   int64_t phase_cycles[9];       /* SM cycles summed over warps per phase of the trajectory
-                                    kernel (contraction, pivoted QR, rank/truncate, split,
-                                    environments, gradients, history copies, layer
-                                    barriers, Jacobi sweeps); zero unless built with
-                                    TNRC_PHASE_TIMERS                                       */
+                                    kernel (contraction, pivoted QR and the second QR,
+                                    rank/truncate, split, environments, gradients, history
+                                    copies, layer barriers, Jacobi sweeps); zero unless
+                                    built with TNRC_PHASE_TIMERS                            */
   int64_t cap_truncations;       /* truncations of the last evaluation (forward and costate
                                     updates) whose cut the cap decided: more singular values
                                     exceeded the cutoff than chi_max keeps (Sec. II, D_max)  */
