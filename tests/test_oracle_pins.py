@@ -838,3 +838,72 @@ def test_per_gate_infidelity_printed_values():
         q = 1 if gate == "X" else 2
         val = robust.per_gate_infidelity(float(chib), int(n), q)
         assert abs(val - float(printed)) < 0.06 * float(printed)
+
+
+# ------------------------------------------- truncation-gap diagnostic (Sec. II)
+def _two_site_state(s, seed):
+    """Two-site state with Schmidt values s (a 2x2 amplitude matrix U diag(s)
+    V^dag), split as B_0 = U diag(s), B_1 = V^dag (the product B_0 B_1 is the
+    amplitude matrix, as the oracle's two-site update reads it)."""
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2)))
+    V, _ = np.linalg.qr(rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2)))
+    B = [(U * s).reshape(1, 2, 2), V.conj().T.reshape(2, 2, 1)]
+    lam = [np.ones(2)]
+    return B, lam
+
+
+def test_gap_at_a_cap_decided_cut_is_the_schmidt_gap():
+    """Keeping one of two Schmidt values (chi = 1) is a cut the cap decides:
+    the gap is (s_1 - s_2) / s_1 of the known spectrum, and the discarded
+    weight s_2^2 / (s_1^2 + s_2^2)."""
+    s = np.array([0.8, 0.6])
+    B, lam = _two_site_state(s, 3)
+    info = {}
+    w, k = mps.two_site_update(B, lam, 0, np.eye(4, dtype=complex), 1, 1e-12, info)
+    assert k == 1
+    assert abs(info["gap"] - (0.8 - 0.6) / 0.8) < 1e-14
+    assert abs(w - 0.36) < 1e-14
+    # the same state kept whole (chi = 2): no cut, no gap
+    B, lam = _two_site_state(s, 3)
+    info = {}
+    w, k = mps.two_site_update(B, lam, 0, np.eye(4, dtype=complex), 2, 1e-12, info)
+    assert k == 2 and info["gap"] is None and abs(w) < 1e-14
+
+
+def test_no_gap_when_the_cutoff_decides():
+    """A second Schmidt value below the cutoff is dropped by the cutoff, not the
+    cap: no gap is reported even at chi = 1."""
+    B, lam = _two_site_state(np.array([1.0, 1e-14]), 4)
+    info = {}
+    _, k = mps.two_site_update(B, lam, 0, np.eye(4, dtype=complex), 1, 1e-12, info)
+    assert k == 1 and info["gap"] is None
+
+
+def test_cut_statistics_are_the_count_and_minimum_of_the_gaps():
+    """Over a trajectory the recorded cap cuts and their smallest gap are those
+    of the individual updates (every update's gap collected separately)."""
+    w = synth.WORKLOADS["ghz30"].replace(N=8, K=3, chi=4, M=1, P=1, u_sigma=1.5, dt=0.25)
+    ins, tgs = w.states()
+    u = w.controls()
+    J = noise.sample_J(w.seed_J, w.M, w.N, w.noise_dist, w.noise_scale)
+    pb = mkpb(w.N, w.K, w.dt, w.C, w.chi, u, w.mask(), J, ins, tgs)
+    gaps = []
+    orig = mps.two_site_update
+
+    def spy(*a, **k):
+        out = orig(*a, **k)
+        info = a[6] if len(a) > 6 else k.get("info")
+        if info is not None and info.get("gap") is not None:
+            gaps.append(info["gap"])
+        return out
+
+    stats = {"discarded": 0.0, "dims": []}
+    try:
+        robust._m.two_site_update = spy
+        robust.trajectory(pb, 0, 0, want_grad=True, stats=stats)
+    finally:
+        robust._m.two_site_update = orig
+    assert len(gaps) > 0
+    assert stats["cap_cuts"] == len(gaps)
+    assert stats["min_gap"] == min(gaps)
