@@ -64,3 +64,25 @@ def test_committed_records_match_the_committed_sources(bench):
         rec = bench.recorded_counters(w)
         assert rec is not None, "profiles/%s is stale for the kernel sources" % f
         assert 0.0 < rec["executed_per_alg"] < 1.0 and rec["bytes_per_slice_step"] > 0.0
+
+
+def test_reference_arm_prints_the_contract_line(bench):
+    """`bench.py --impl reference` (the CPU oracle timed on a bounded sample of
+    the benchmark workload) prints one JSON line with the GPU arm's metric,
+    unit and config, its own cpu_baseline and a zero-copy e2e block."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(HERE, "..", "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=os.path.join(HERE, ".."))
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0 and d["n_gpus"] == 1
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    assert d["config"]["workload"].startswith("cnot50") and d["config"]["slice_steps_per_eval"] == 204800
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
