@@ -133,3 +133,46 @@ def test_footprint_follows_the_discretisation_and_form(L):
     assert tnrc.footprint(*args, substeps=3) > base
     assert tnrc.footprint(*args, operator=True) > base
     assert tnrc.footprint(*args, order=1) > 0
+
+
+def _static_case(w):
+    from oracle import noise
+    ins, tgs = w.states()
+    J = noise.sample_J(w.seed_J, w.M, w.N, w.noise_dist, w.noise_scale, terms=w.crosstalk)
+    return ins, tgs, w.controls(), J, w.mask()
+
+
+def test_static_entry_validates_on_the_host(L):
+    """tnrc_fidelity_static checks the problem, its arrays and its size
+    against the static array on the host, before any device call: an
+    oversize problem is TNRC_E_TOO_LARGE, non-finite controls, noise or
+    fixed couplings TNRC_E_INVALID, on a machine with or without a GPU."""
+    from paper_2603_03639_gb300 import tnrc
+    import synth
+    w = synth.WORKLOADS["cnot50"].replace(M=64)
+    ins, tgs, u, J, mask = _static_case(w)
+    with pytest.raises(tnrc.TNRCError) as e:
+        tnrc.fidelity_static(w.N, w.K, w.dt, w.chi, w.C, ins, tgs, u, J, mask=mask)
+    assert e.value.status == -7
+    w = synth.WORKLOADS["x8"].replace(M=2)
+    ins, tgs, u, J, mask = _static_case(w)
+    for bad_u, bad_J, gfix in ((np.where(np.arange(u.size).reshape(u.shape) == 5, np.nan, u), J, None),
+                               (u, np.where(np.arange(J.size).reshape(J.shape) == 3, np.inf, J), None),
+                               (u, J, np.full((w.K, w.N - 1), np.inf))):
+        with pytest.raises(tnrc.TNRCError) as e:
+            tnrc.fidelity_static(w.N, w.K, w.dt, w.chi, w.C, ins, tgs, bad_u, bad_J, mask=mask, g_fixed=gfix)
+        assert e.value.status == -1
+
+
+def test_static_entry_without_a_device_reports_cuda_error(L):
+    """A valid problem on a machine without a GPU: TNRC_E_CUDA, no crash."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2603_03639_gb300 import tnrc
+    import synth
+    w = synth.WORKLOADS["x8"].replace(M=2)
+    ins, tgs, u, J, mask = _static_case(w)
+    with pytest.raises(tnrc.TNRCError) as e:
+        tnrc.fidelity_static(w.N, w.K, w.dt, w.chi, w.C, ins, tgs, u, J, mask=mask)
+    assert e.value.status == -3
